@@ -1,0 +1,268 @@
+"""FP64 CPU oracle of the phase-field LBM coupled step (arXiv 2012.14729, Sec. 3).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, plain reference the CUDA
+path is checked against; only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import it.  It shares no code with the CUDA library.
+
+The arithmetic lives in ``pflbm_oracle.c`` (plain loops, double precision,
+whole-grid passes in the order of the scheme); this module compiles it with
+gcc, calls it through ctypes, and adds the FP64 diagnostics of Sec. 5
+(Laplace pressure jump, spurious currents, mass, mass centre, Taylor
+deformation), written with numpy.
+
+Parity of every function here is pinned by ``tests/test_oracle_*.py``
+against moment identities, closed forms, invariants and physical laws.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pflbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+FORMS = ("STF1", "STF2", "CPF1", "CPF2", "PF1", "PF2", "CSF1", "CSF2")
+FAMILY = {"STF": "STF1", "CPF": "CPF1", "PF": "PF1", "CSF": "CSF1"}
+
+# parameter vector layout shared with pflbm_oracle.c (P_* enum there)
+_PAR = ("sigma", "W", "M", "tau_h", "rho1", "rho2", "nu1", "nu2", "gx", "gy",
+        "rho0", "uw_bottom", "uw_top", "eps", "form")
+# macro field block layout (M_* enum in pflbm_oracle.c)
+FIELDS = ("phi", "gx", "gy", "lap", "mu", "Fx", "Fy", "rho", "ux", "uy", "P",
+          "phiux", "phiuy", "div_phiu", "dt_phiux", "dt_phiuy", "tau_f", "p_h")
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP,
+    no FMA contraction so results do not depend on the host ISA)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-std=c99", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i = ctypes.c_int
+        d = ctypes.c_double
+        _lib.orc_feq.argtypes = [d, d, d, d, dp]
+        _lib.orc_heq.argtypes = [d, d, d, d, d, dp]
+        _lib.orc_fforce.argtypes = [d, d, d, d, d, d, dp]
+        _lib.orc_hsource.argtypes = [d, d, d, d, dp]
+        _lib.orc_macro.argtypes = [dp, i, i, i, dp, dp, dp, i, dp]
+        _lib.orc_step.argtypes = [dp, i, i, i, dp, dp, dp, i, i]
+        _lib.orc_init.argtypes = [dp, i, i, i, dp, dp, dp, dp]
+        _lib.orc_ics.argtypes = [i, i, i, dp, dp]
+        assert _lib.orc_nfields() == len(FIELDS)
+        assert _lib.orc_npar() == len(_PAR)
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def set_threads(n: int) -> None:
+    """Threads the oracle's OpenMP loops use (results do not depend on it)."""
+    os.environ["OMP_NUM_THREADS"] = str(n)
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+    except OSError:
+        pass
+
+
+@dataclass
+class Params:
+    """Physical parameters in lattice units (delta x = delta t = 1).
+
+    sigma, W        surface tension and interface width (beta = 3 sigma / 4W,
+                    kappa = 3 W sigma / 8, Sec. 2.1)
+    M, tau_h        mobility and CH relaxation time (M = cs^2 eta (tau_h - 1/2))
+    rho1, rho2      densities of fluid 1 (phi = +1) and fluid 2 (phi = -1)
+    nu1, nu2        kinematic viscosities (mu_k = rho_k nu_k)
+    gx, gy          gravity; F_g = (rho - rho0) g
+    rho0            background density; NaN means the mean of rho(phi0)
+    uw_bottom/top   x-velocity of the walls at y = -1/2 and y = ny - 1/2
+    eps             regularisation of the CSF normal
+    form            interfacial force formulation, one of FORMS
+    """
+    sigma: float = 0.01
+    W: float = 4.0
+    M: float = 0.1
+    tau_h: float = 1.0
+    rho1: float = 1.0
+    rho2: float = 1.0
+    nu1: float = 0.1
+    nu2: float = 0.1
+    gx: float = 0.0
+    gy: float = 0.0
+    rho0: float = float("nan")
+    uw_bottom: float = 0.0
+    uw_top: float = 0.0
+    eps: float = 1e-6
+    form: str = "STF1"
+
+    def vector(self) -> np.ndarray:
+        v = []
+        for k in _PAR:
+            val = getattr(self, k)
+            if k == "form":
+                val = FORMS.index(FAMILY.get(val, val))
+            v.append(float(val))
+        return np.array(v, dtype=np.float64)
+
+
+def feq(P, rho, ux, uy):
+    out = np.zeros(9)
+    lib().orc_feq(P, rho, ux, uy, _p(out))
+    return out
+
+
+def heq(phi, mu, eta, ux, uy):
+    out = np.zeros(9)
+    lib().orc_heq(phi, mu, eta, ux, uy, _p(out))
+    return out
+
+
+def fforce(ux, uy, Fx, Fy, drx, dry):
+    out = np.zeros(9)
+    lib().orc_fforce(ux, uy, Fx, Fy, drx, dry, _p(out))
+    return out
+
+
+def hsource(tau_h, divphiu, dtx, dty):
+    out = np.zeros(9)
+    lib().orc_hsource(tau_h, divphiu, dtx, dty, _p(out))
+    return out
+
+
+def ics(a: np.ndarray, wall: bool = False):
+    """Central-scheme gradient and Laplacian of a [ny][nx] field."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ny, nx = a.shape
+    out = np.zeros((3, ny, nx))
+    lib().orc_ics(nx, ny, int(wall), _p(a), _p(out))
+    return out[0], out[1], out[2]
+
+
+def mean_rho(par: Params, phi0: np.ndarray) -> float:
+    """Default background density: the domain mean of rho(phi0)."""
+    rho = par.rho1 * 0.5 * (1 + phi0) + par.rho2 * 0.5 * (1 - phi0)
+    return float(np.mean(rho))
+
+
+class Sim:
+    """One oracle run: pre-collision populations f, h at the current time,
+    (phi u) of the previous step, and the step counter."""
+
+    def __init__(self, nx: int, ny: int, wall_y: bool, par: Params, phi0: np.ndarray):
+        self.nx, self.ny, self.wall = int(nx), int(ny), bool(wall_y)
+        phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(ny, nx)
+        if math.isnan(par.rho0):
+            par = Params(**{**par.__dict__, "rho0": mean_rho(par, phi0)})
+        self.par = par
+        self.pv = par.vector()
+        self.f = np.zeros((9, ny, nx))
+        self.h = np.zeros((9, ny, nx))
+        self.phiu_prev = np.zeros((2, ny, nx))
+        lib().orc_init(_p(self.pv), nx, ny, int(self.wall), _p(phi0), _p(self.f),
+                       _p(self.h), _p(self.phiu_prev))
+        self.t = 0
+
+    def step(self, n: int = 1) -> "Sim":
+        if n > 0:
+            lib().orc_step(_p(self.pv), self.nx, self.ny, int(self.wall), _p(self.f),
+                           _p(self.h), _p(self.phiu_prev), int(n), int(self.t == 0))
+            self.t += n
+        return self
+
+    def macro(self) -> dict:
+        out = np.zeros((len(FIELDS), self.ny, self.nx))
+        lib().orc_macro(_p(self.pv), self.nx, self.ny, int(self.wall), _p(self.f),
+                        _p(self.h), _p(self.phiu_prev), int(self.t == 0), _p(out))
+        return {k: out[i] for i, k in enumerate(FIELDS)}
+
+
+# ---------------------------------------------------------------------------
+# FP64 diagnostics (Sec. 5)
+# ---------------------------------------------------------------------------
+
+def laplace(fields: dict, xc: float, yc: float, R: float, W: float) -> dict:
+    """Laplace-law measurement (Sec. 5.1): R_num from the drop area, Delta p as
+    the mean hydrodynamic pressure p_h inside r <= R/2 minus its mean outside
+    r >= R + 3W (periodic distance from the initial centre),
+    sigma_num = R_num Delta p."""
+    phi, P = fields["phi"], fields["p_h"]
+    ny, nx = phi.shape
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    dx = np.abs(x - xc)
+    dx = np.minimum(dx, nx - dx)
+    dy = np.abs(y - yc)
+    dy = np.minimum(dy, ny - dy)
+    r = np.sqrt(dx * dx + dy * dy)
+    inside = r <= R / 2
+    outside = r >= R + 3 * W
+    area = float(np.sum(0.5 * (1 + phi)))
+    R_num = math.sqrt(area / math.pi)
+    dp = float(P[inside].mean() - P[outside].mean())
+    return {"R_num": R_num, "dp": dp, "sigma_num": R_num * dp}
+
+
+def umax(fields: dict) -> float:
+    return float(np.sqrt(fields["ux"] ** 2 + fields["uy"] ** 2).max())
+
+
+def mass(fields: dict) -> float:
+    return float(np.sum(fields["phi"]))
+
+
+def mass_centre_x(fields: dict) -> float:
+    """x_c of fluid 1 (weight (1 + phi)/2), Sec. 5.2."""
+    w = 0.5 * (1 + fields["phi"])
+    nx = w.shape[1]
+    x = np.arange(nx)[None, :]
+    return float(np.sum(w * x) / np.sum(w))
+
+
+def taylor_D(fields: dict) -> float:
+    """Taylor deformation D = (L - B)/(L + B) (Sec. 5.5), with L, B read as
+    4 sqrt(lambda) of the second-moment matrix of w = (1 + phi)/2 about its
+    centroid (twice the semi-axes of the equivalent ellipse)."""
+    w = 0.5 * (1 + fields["phi"])
+    ny, nx = w.shape
+    x = np.arange(nx)[None, :] + 0.0 * w
+    y = np.arange(ny)[:, None] + 0.0 * w
+    m = w.sum()
+    cx, cy = (w * x).sum() / m, (w * y).sum() / m
+    sxx = (w * (x - cx) ** 2).sum() / m
+    syy = (w * (y - cy) ** 2).sum() / m
+    sxy = (w * (x - cx) * (y - cy)).sum() / m
+    tr, det = sxx + syy, sxx * syy - sxy * sxy
+    disc = math.sqrt(max(tr * tr / 4 - det, 0.0))
+    l1, l2 = tr / 2 + disc, tr / 2 - disc
+    L, B = 4 * math.sqrt(l1), 4 * math.sqrt(max(l2, 0.0))
+    return (L - B) / (L + B)

@@ -1,0 +1,184 @@
+"""Oracle pins: closed forms and physical laws the method must reproduce.
+
+  - every force formulation (Eqs. SF1, SF2, SF3456, SF7, SF8) converges at
+    second order to its continuum expression, evaluated with exact symbolic
+    derivatives of a smooth drop profile (sympy, independent of the stencils);
+  - the plane interface keeps the tanh profile of width W (Eq.
+    equilibrium_profile) up to the O(dx^2) error of the discrete chemical
+    potential;
+  - Laplace's law Delta p = sigma / R for a stationary drop (Sec. 5.1), for
+    every form, within the band of errors the paper reports (Table
+    test1_laplace, up to 7.9 %);
+  - a small sinusoidal perturbation of phi = 1 decays at the linearised
+    Cahn-Hilliard rate M k^2 (8 beta + kappa k^2) (Eqs. CH, chemical_potential,
+    with M = cs^2 eta (tau_h - 1/2));
+  - a shear wave decays at nu k^2 with nu = cs^2 (tau_f - 1/2).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2012_14729_gb300 import workloads as wl
+
+FORMS = ("STF1", "STF2", "CPF1", "CPF2", "PF1", "PF2", "CSF1", "CSF2")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _continuum_forces(n, R, W, sigma):
+    """Exact interfacial forces of the drop phi = tanh(2 (R - r)/W) at the
+    grid nodes, from symbolic derivatives."""
+    sp = pytest.importorskip("sympy")
+    x, y = sp.symbols("x y", real=True)
+    xc = yc = n / 2
+    r = sp.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    phi = sp.tanh(2 * (R - r) / W)
+    beta = sp.Rational(3, 4) * sigma / W
+    kap = sp.Rational(3, 8) * W * sigma
+    gx, gy = sp.diff(phi, x), sp.diff(phi, y)
+    lap = sp.diff(phi, x, 2) + sp.diff(phi, y, 2)
+    mu = 4 * beta * phi * (phi ** 2 - 1) - kap * lap
+    g2 = gx ** 2 + gy ** 2
+    gabs = sp.sqrt(g2)
+    nx_, ny_ = gx / gabs, gy / gabs
+    divn = sp.diff(nx_, x) + sp.diff(ny_, y)
+    div_t = (sp.diff(gx * gx, x) + sp.diff(gx * gy, y), sp.diff(gx * gy, x) + sp.diff(gy * gy, y))
+    F = {
+        "STF1": (-kap * div_t[0], -kap * div_t[1]),
+        "STF2": (kap * sp.diff(g2, x) - kap * div_t[0], kap * sp.diff(g2, y) - kap * div_t[1]),
+        "CPF1": (-phi * sp.diff(mu, x), -phi * sp.diff(mu, y)),
+        "CPF2": (mu * gx, mu * gy),
+        "PF1": (-kap * gx * lap, -kap * gy * lap),
+        "PF2": (kap * phi * sp.diff(lap, x), kap * phi * sp.diff(lap, y)),
+        "CSF1": (-kap * gx * gabs * divn, -kap * gy * gabs * divn),
+        "CSF2": (-sigma / 2 * gx * divn, -sigma / 2 * gy * divn),
+    }
+    Y, X = np.mgrid[0:n, 0:n].astype(float)
+    out = {}
+    for k, (fx, fy) in F.items():
+        fxn = sp.lambdify((x, y), fx, "numpy")
+        fyn = sp.lambdify((x, y), fy, "numpy")
+        out[k] = (np.asarray(fxn(X, Y), dtype=float), np.asarray(fyn(X, Y), dtype=float))
+    phin = sp.lambdify((x, y), phi, "numpy")(X, Y)
+    return out, phin
+
+
+@pytest.fixture(scope="module")
+def continuum():
+    import warnings
+    warnings.filterwarnings("ignore", category=RuntimeWarning)
+    res = {}
+    for W in (8.0, 16.0):
+        n, R = int(16 * W), 4 * W
+        res[W] = (n, R) + _continuum_forces(n, R, W, 0.01)
+    return res
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_force_forms_converge_to_continuum(orc, continuum, form):
+    errs = []
+    for W in (8.0, 16.0):
+        n, R, exact, phin = continuum[W]
+        s = orc.Sim(n, n, False, orc.Params(sigma=0.01, W=W, form=form), phin)
+        m = s.macro()
+        band = np.abs(phin) < 0.9
+        fx, fy = exact[form]
+        num = np.hypot(m["Fx"] - fx, m["Fy"] - fy)[band]
+        ref = np.hypot(fx, fy)[band]
+        errs.append(np.sqrt((num ** 2).sum() / (ref ** 2).sum()))
+    # W = 8 -> 16 halves the cell size relative to the profile
+    assert errs[1] < 0.1, errs
+    assert errs[0] / errs[1] > 3.4, errs
+
+
+def test_equilibrium_forms_coincide(orc, continuum):
+    """On the equilibrium drop profile STF-2, CPF-2 and CSF-1 coincide (Eq.
+    relationSF7-simplify): their discrete differences shrink at second order,
+    while STF-1 stays apart by the gradient term grad(kappa |grad phi|^2)."""
+    def rel(a, b):
+        return np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+    d = {}
+    for W in (8.0, 16.0):
+        n, R, exact, phin = continuum[W]
+        F = {}
+        for form in ("STF1", "STF2", "CPF2", "CSF1"):
+            m = orc.Sim(n, n, False, orc.Params(sigma=0.01, W=W, form=form), phin).macro()
+            F[form] = np.stack([m["Fx"], m["Fy"]])
+        d[W] = {k: rel(F[k], F["CSF1"]) for k in ("STF1", "STF2", "CPF2")}
+    assert d[16.0]["STF2"] < 0.02 and d[16.0]["CPF2"] < 0.06
+    assert d[8.0]["STF2"] / d[16.0]["STF2"] > 3.0
+    assert d[8.0]["CPF2"] / d[16.0]["CPF2"] > 3.0
+    assert d[16.0]["STF1"] > 1.0
+
+
+def test_tanh_profile_is_equilibrium(orc):
+    errs = []
+    for W in (4.0, 8.0):
+        n = int(16 * W)
+        x = np.arange(n)[None, :] + 0 * np.arange(4)[:, None]
+        ex = np.tanh(2 * (n / 4 - np.abs(x - n / 2)) / W)
+        s = orc.Sim(n, 4, False, orc.Params(sigma=0.05, W=W, M=0.2, form="CPF2"), ex)
+        s.step(int(5000 * (W / 4) ** 2))
+        errs.append(np.abs(s.macro()["phi"] - ex).max())
+    assert errs[0] < 0.02 and errs[1] < 0.005
+    assert errs[0] / errs[1] > 3.5
+
+
+def _paper_band():
+    with open(os.path.join(GOLDEN, "laplace_table.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_laplace_law(orc, form):
+    """64^2 stationary drop R = 16, W = 4, sigma = 0.01 (the stationary-drop
+    workload) after 5000 steps: |sigma_num - sigma| / sigma must lie inside
+    the band the paper reports over all forms and grids."""
+    band = _paper_band()
+    worst = max(max(v) for v in band["err_percent"].values())
+    c = wl.stationary_drop(form)
+    s = orc.Sim(c.nx, c.ny, False, orc.Params(**c.params), c.phi0)
+    s.step(5000)
+    L = orc.laplace(s.macro(), 32, 32, 16.0, 4.0)
+    err = abs(L["sigma_num"] - 0.01) / 0.01 * 100
+    assert err < worst + 0.5, (form, err)
+
+
+def test_phi_mode_decay_rate(orc):
+    res = []
+    for n in (32, 64):
+        sigma, W, M = 0.1, 4.0, 0.1
+        beta, kap = 0.75 * sigma / W, 0.375 * W * sigma
+        x = np.arange(n)[None, :] + 0 * np.arange(4)[:, None]
+        k = 2 * math.pi / n
+        s = orc.Sim(n, 4, False, orc.Params(sigma=sigma, W=W, M=M, form="STF1"),
+                    1 + 1e-5 * np.cos(k * x))
+        s.step(10)
+        a0 = (s.macro()["phi"][0] - 1) @ np.cos(k * np.arange(n))
+        s.step(500)
+        a1 = (s.macro()["phi"][0] - 1) @ np.cos(k * np.arange(n))
+        rate = -math.log(a1 / a0) / 500
+        res.append(rate / (M * k * k * (8 * beta + kap * k * k)) - 1)
+    assert abs(res[0]) < 5e-3 and abs(res[1]) < 1.5e-3
+    assert abs(res[0] / res[1]) > 3.0
+
+
+def test_shear_wave_viscosity(orc):
+    res = []
+    for n in (32, 64):
+        nu = 0.1
+        s = orc.Sim(4, n, False, orc.Params(nu1=nu, nu2=nu), np.ones((n, 4)))
+        y = np.arange(n)
+        k = 2 * math.pi / n
+        U = 1e-4 * np.sin(k * y)
+        for yy in range(n):
+            s.f[:, yy, :] = orc.feq(0.0, 1.0, U[yy], 0.0)[:, None]
+        s.step(5)
+        a0 = s.macro()["ux"][:, 0] @ np.sin(k * y)
+        s.step(400)
+        a1 = s.macro()["ux"][:, 0] @ np.sin(k * y)
+        res.append(-math.log(a1 / a0) / 400 / (nu * k * k) - 1)
+    assert abs(res[0]) < 4e-3 and abs(res[1]) < 1e-3
+    assert abs(res[0] / res[1]) > 3.0
