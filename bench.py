@@ -1,0 +1,338 @@
+"""Throughput of the fused phase-field LBM step on GB300, one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--form F] [--storage fp32|fp16|bf16]
+
+Metric: GLUPS = (lattice nodes x time steps) / second, one coupled f + h
+update per node and step.  A step is one pass of the whole hot path: one
+fused kernel launch (moments, central-scheme derivatives, interfacial force,
+collision and streaming of both D2Q9 populations) over the workload's grid.
+
+Default workload: the plain-FP32 capillary-wave / rising-bubble configuration
+at scale, 512 x 1024 nodes, walls at bottom and top, rising bubble R = 64,
+W = 5, sigma = 1e-3, M = 0.05, g = 1e-6, seeded 1e-3 noise on phi0 (density
+ratio 10 with equal kinematic viscosities: the stated ratio 1000 diverges).
+Its state (84 MB double-buffered) fits in the 129 MB L2, so L2 is flushed by
+writing a 256 MB buffer before every timed step; each step is timed with CUDA
+events on the domain's stream around its single kernel launch.
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own replica
+of the workload, no data-path collective (the instances are independent);
+value = all ranks' node-steps / max over ranks of the time ("scaling":
+"weak").
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2012_14729_gb300 import workloads as wl  # noqa: E402
+
+BYTES_PER_LUP = {"fp32": 160, "fp16": 92, "bf16": 92}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def make_case(name: str, form: str):
+    if name == "bubble_512x1024":
+        return wl.capillary_bubble("bubble", form=form)
+    if name == "wave_512x1024":
+        return wl.capillary_bubble("wave", form=form)
+    if name == "bubble_4096x2048":
+        # same physics as the default at 8x the nodes (state 1.3 GB > L2)
+        return wl.capillary_bubble("bubble", form=form, nx=2048, ny=4096, R=256.0)
+    if name == "drop_64x64":
+        return wl.stationary_drop(form)
+    if name == "merging_256x128":
+        return wl.merging_drops(form)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record(storage: str):
+    """DRAM bytes per node and step of the step kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2012_14729_gb300", "csrc", "step_kernel.cuh")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        r = rec.get(storage)
+        if r and r.get("kernel_sha") == sha:
+            return float(r["dram_bytes_per_lup"])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[4:8]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2):
+    """Oracle steps on the full grid of the workload until `seconds` of CPU
+    work: returns (GLUPS, steps, threads)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0)
+    s.step(1)  # first step separately (first-step flag), untimed
+    t0 = time.perf_counter()
+    n = 0
+    while n < min_steps or (time.perf_counter() - t0 < seconds and n < max_steps):
+        s.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return case.nx * case.ny * n / dt / 1e9, n, threads
+
+
+def run_reference(args, case):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = case.nx * case.ny * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "GLUPS (coupled f+h step)", "value": value,
+        "unit": "GLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nx": case.nx, "ny": case.ny,
+                   "form": args.form, "walls": "y" if case.wall_y else "none"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.warmup}+{args.steps} full-grid oracle steps"},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, case):
+    import torch
+    from paper_2012_14729_gb300 import build, pflbm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build()
+    pflbm.load()
+
+    n_nodes = case.nx * case.ny
+    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage, device=dev)
+    dom.set_params(**case.params)
+    dom.init_phi(case.phi0.astype(np.float32))
+    stream = dom.stream
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            dom.step(1)
+    stream.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        with torch.cuda.stream(stream):
+            for e0, e1 in evs:
+                flush.zero_()          # cold L2 for every timed step
+                e0.record(stream)
+                dom.step(1)            # one fused kernel launch
+                e1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    per_step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    t_ms = sum(per_step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    value = ws * n_nodes * args.steps / (t_ms * 1e-3) / 1e9
+
+    # stability check of the state that was timed (not timed)
+    diag = dom.diagnostics()
+
+    # end to end through the public API with host buffers: phi0 from pinned
+    # host memory, K steps, all fields back to pinned host memory
+    phi_host = torch.from_numpy(case.phi0.astype(np.float32)).pin_memory()
+    out_host = torch.empty((len(pflbm.FIELDS), case.ny, case.nx), dtype=torch.float32,
+                           pin_memory=True)
+    e2e_dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage,
+                           device=dev, stream=stream)
+    e2e_dom.set_params(**case.params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pflbm.pflbm_init_phi(e2e_dom.h, phi_host)
+    pflbm.pflbm_step(e2e_dom.h, args.steps)
+    pflbm.pflbm_read_fields(e2e_dom.h, out_host)
+    stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": ws * n_nodes * args.steps / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": n_nodes * 4 / args.steps,
+           "d2h_bytes_per_step": len(pflbm.FIELDS) * n_nodes * 4 / args.steps}
+
+    peak, peak_kind = measured_peaks()
+    bpl = BYTES_PER_LUP[args.storage]
+    launch_ms = statistics.mean(per_step_ms)
+    achieved = bpl * n_nodes / (launch_ms * 1e-3) / 1e9
+    tr = traffic_record(args.storage)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": None if tr is None else tr * n_nodes,
+                "algorithmic_bytes": bpl * n_nodes, "kernel": "k_step"}
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        v, n, thr = oracle_sample(case, seconds=args.cpu_seconds)
+        cpu = {"value": v, "unit": "GLUPS", "cores": thr, "kind": "oracle",
+               "sample": f"{n} full-grid FP64 oracle steps of {args.workload}"}
+
+    line = {
+        "metric": "GLUPS (coupled f+h step)", "value": value, "unit": "GLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "nx": case.nx, "ny": case.ny,
+                   "walls": "y" if case.wall_y else "none", "form": args.form,
+                   "storage": args.storage, "l2": "flushed before every timed step",
+                   "parallelism": f"replicas{ws}", "state_status": diag["status"]},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="bubble_512x1024")
+    ap.add_argument("--form", default="STF1")
+    ap.add_argument("--storage", default="fp32", choices=("fp32", "fp16", "bf16"))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    case = make_case(args.workload, args.form)
+    if args.impl == "reference":
+        run_reference(args, case)
+    else:
+        run_ours(args, case)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * pflbm.h — C ABI of the GB300 (sm_103a) phase-field lattice Boltzmann step.
+ *
+ * The library advances the coupled D2Q9 populations of the phase-field
+ * lattice Boltzmann method of Zhang, Liang & Guo (arXiv 2012.14729, Sec. 3):
+ * the pressure-based flow populations f_i (He et al.) and the order-parameter
+ * populations h_i (improved Cahn-Hilliard scheme), with the interfacial force
+ * in any of the paper's eight formulations (Sec. 2.2) and half-way
+ * bounce-back walls (Sec. 4).  One call of pflbm_step runs the fused CUDA
+ * kernel once per time step on the caller's stream.
+ *
+ * Conventions shared by every entry point
+ *   - Units: lattice units, delta x = delta t = 1, cs^2 = 1/3.
+ *   - Layout of every field a caller passes or receives: float32, row-major
+ *     [ny][nx], x fastest; population blocks are [9][ny][nx] in the D2Q9 order
+ *     c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+ *   - Phases: phi = +1 in fluid 1, phi = -1 in fluid 2 (Sec. 2.1).
+ *   - Ownership: the caller owns the device workspace (its size from
+ *     pflbm_workspace_bytes), the CUDA stream and every input/output buffer.
+ *     The library allocates no device memory and keeps no caller pointer
+ *     beyond a call, except the workspace and stream given to pflbm_create,
+ *     which must outlive the handle.  The handle itself is host memory
+ *     released by pflbm_destroy.
+ *   - Pointers flagged `on_device` are device pointers when the flag is
+ *     nonzero and host pointers otherwise.
+ *   - Asynchrony: pflbm_step only enqueues work on the stream.  Calls that
+ *     return data to a host buffer (read, diagnostics, save_state to host)
+ *     synchronise the stream before returning.
+ *   - Errors: every call returns a pflbm_status; PFLBM_ECUDA carries the CUDA
+ *     error text in pflbm_last_error().  Nothing aborts the process.
+ *   - Threads: one handle must not be used from two host threads at once;
+ *     distinct handles are independent.
+ */
+#ifndef PFLBM_H
+#define PFLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pflbm_domain pflbm_domain;
+
+typedef enum {
+  PFLBM_OK = 0,
+  PFLBM_EINVAL = 1,     /* bad argument or parameter */
+  PFLBM_ENOMEM_WS = 2,  /* workspace smaller than pflbm_workspace_bytes */
+  PFLBM_ECUDA = 3,      /* a CUDA call failed, see pflbm_last_error() */
+  PFLBM_EUNSTABLE = 4,  /* a diagnostic found NaN or Inf in the state */
+  PFLBM_ETIMEOUT = 5,   /* a bounded device wait expired */
+  PFLBM_ESTATE = 6      /* call out of order (no params / no initial phi) */
+} pflbm_status;
+
+typedef enum { PFLBM_PERIODIC = 0, PFLBM_WALL = 1 } pflbm_bc;
+
+/* Interfacial force formulations (Sec. 2.2):
+ *   STF1  -div(kappa grad phi (x) grad phi)                    Eq. SF1
+ *   STF2  div(kappa(|grad phi|^2 I - grad phi (x) grad phi))   Eq. SF2
+ *   CPF1  -phi grad mu,   CPF2  mu grad phi                    Eq. SF3456
+ *   PF1   -kappa grad phi lap phi, PF2 kappa phi grad lap phi  Eq. SF3456
+ *   CSF1  -kappa grad phi |grad phi| div n                     Eq. SF7
+ *   CSF2  -(sigma/2) grad phi div n                            Eq. SF8
+ * A family name alone means its first variant. */
+typedef enum {
+  PFLBM_STF1 = 0, PFLBM_STF2 = 1, PFLBM_CPF1 = 2, PFLBM_CPF2 = 3,
+  PFLBM_PF1 = 4, PFLBM_PF2 = 5, PFLBM_CSF1 = 6, PFLBM_CSF2 = 7,
+  PFLBM_STF = PFLBM_STF1, PFLBM_CPF = PFLBM_CPF1, PFLBM_PF = PFLBM_PF1,
+  PFLBM_CSF = PFLBM_CSF1
+} pflbm_force;
+
+/* How populations are stored in HBM.  Arithmetic is float32 in every case.
+ * FP16/BF16 store f_i and h_1..h_8 as 16-bit scaled deviations from the rest
+ * state (f^rest = 0, h_i^rest = 0 for i > 0), i.e. p_i / w_i * scale, and keep
+ * h_0 (which carries phi) in float32. */
+typedef enum { PFLBM_FP32 = 0, PFLBM_FP16 = 1, PFLBM_BF16 = 2 } pflbm_storage;
+
+/* Fields of pflbm_read, all at the current time level (Eq. mac):
+ * phi, rho, u_x, u_y, generalised pressure P_sf, chemical potential mu,
+ * hydrodynamic pressure p_h (P_sf minus the gradient terms of the chosen
+ * form, Eqs. SF1, SF2, P3456), interfacial + gravity force F_x, F_y. */
+typedef enum {
+  PFLBM_PHI = 0, PFLBM_RHO = 1, PFLBM_UX = 2, PFLBM_UY = 3, PFLBM_P = 4,
+  PFLBM_MU = 5, PFLBM_PH = 6, PFLBM_FX = 7, PFLBM_FY = 8, PFLBM_NFIELDS = 9
+} pflbm_field;
+
+/* Physical parameters in lattice units (Sec. 2.1, Sec. 3):
+ *   sigma, W       surface tension and interface width; beta = 3 sigma/(4W),
+ *                  kappa = 3 W sigma / 8
+ *   M, tau_h       mobility and CH relaxation time; eta = M / (cs^2 (tau_h - 1/2))
+ *   rho1, rho2     densities of fluid 1 (phi = +1) and fluid 2 (phi = -1)
+ *   nu1, nu2       kinematic viscosities; tau_f = 1/2 + mu(phi) / (rho cs^2)
+ *   gx, gy         gravity, F_g = (rho - rho0) g
+ *   rho0           background density; NaN selects the domain mean of rho(phi0)
+ *   uw_bottom/top  x-velocity of the walls at y = -1/2 and y = ny - 1/2
+ *   eps            regularisation of the CSF normal n = grad phi / sqrt(|grad phi|^2 + eps^2)
+ *   force          a pflbm_force
+ *   scale_f, scale_h  16-bit storage scales (powers of two); 0 selects 2^round(log2(4/sigma)) */
+typedef struct {
+  double sigma, W, M, tau_h;
+  double rho1, rho2, nu1, nu2;
+  double gx, gy, rho0;
+  double uw_bottom, uw_top;
+  double eps;
+  int32_t force;
+  int32_t reserved;
+  double scale_f, scale_h;
+} pflbm_params;
+
+/* Geometry of the Laplace-law measurement (Sec. 5.1): the pressure jump is
+ * the mean p_h over nodes within r_in of (xc, yc) minus the mean over nodes
+ * farther than r_out (periodic distances). */
+typedef struct {
+  double xc, yc, r_in, r_out;
+} pflbm_diag_geom;
+
+/* FP64 diagnostics of the current state (Secs. 5.1, 5.2, 5.5). */
+typedef struct {
+  double mass;        /* sum phi (conserved exactly in exact arithmetic) */
+  double umax;        /* max |u| (spurious currents) */
+  double area1;       /* sum (1 + phi)/2: area of fluid 1 */
+  double R_num;       /* sqrt(area1 / pi) */
+  double p_in, p_out; /* mean p_h inside r_in / outside r_out */
+  double dp;          /* p_in - p_out */
+  double sigma_num;   /* R_num * dp (Laplace law) */
+  double xc1, yc1;    /* centroid of fluid 1 (weight (1 + phi)/2) */
+  double taylor_D;    /* (L - B)/(L + B), L, B = 4 sqrt(eigenvalues of the
+                         second-moment matrix of (1 + phi)/2) */
+  double nonfinite;   /* number of nodes with a NaN/Inf field */
+} pflbm_diag;
+
+/* ---- domain ------------------------------------------------------------ */
+
+/* Bytes of device workspace a domain of nx x ny with this storage needs
+ * (populations double-buffered with one ghost row above and below, phi u,
+ * field staging and reduction scratch).  0 for invalid sizes. */
+size_t pflbm_workspace_bytes(int nx, int ny, pflbm_storage storage);
+
+/* Create a domain over a caller-owned device workspace (256-byte aligned,
+ * at least pflbm_workspace_bytes) and CUDA stream (cudaStream_t, NULL = the
+ * legacy default stream).  bc_x must be PFLBM_PERIODIC; bc_y may be either.
+ * nx, ny >= 4.  The domain (Sec. 5 benchmarks) is the paper's uniform
+ * L_x x L_y lattice.  Errors: EINVAL, ENOMEM_WS. */
+pflbm_status pflbm_create(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y,
+                          pflbm_storage storage, void* dev_workspace,
+                          size_t ws_bytes, void* cuda_stream, pflbm_domain** out);
+
+/* Set the physical parameters (copied).  Rejects sigma < 0, W <= 0, M <= 0,
+ * tau_h <= 1/2, non-positive densities or viscosities, eps < 0, an unknown
+ * force, and non-power-of-two storage scales, with EINVAL. */
+pflbm_status pflbm_set_params(pflbm_domain* d, const pflbm_params* p);
+
+/* Initial state (Sec. 5.1: zero velocity): f = f^eq(P = 0, u = 0) = 0 and
+ * h = h^eq(phi0, mu0, u = 0), mu0 the chemical potential of phi0
+ * (Eq. chemical_potential).  phi0: [ny][nx] float32.  Resets the step count.
+ * Errors: ESTATE without params, ECUDA. */
+pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device);
+
+/* Advance nsteps time steps (Eqs. fh; one fused kernel per step), enqueued
+ * on the stream.  With graphs enabled the steps after the first replay a
+ * captured CUDA graph.  Errors: ESTATE before init, ECUDA. */
+pflbm_status pflbm_step(pflbm_domain* d, int nsteps);
+
+/* Use captured CUDA graphs for pflbm_step (1) or plain launches (0, the
+ * default).  Graphs need a non-default stream. */
+pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
+
+/* Steps taken since pflbm_init_phi. */
+long long pflbm_steps_done(const pflbm_domain* d);
+
+/* One field at the current time level into dst [ny][nx] (synchronises when
+ * dst is on the host).  Errors: EINVAL for an unknown field, ESTATE, ECUDA. */
+pflbm_status pflbm_read(pflbm_domain* d, pflbm_field field, float* dst, int on_device);
+
+/* All PFLBM_NFIELDS fields into dst [PFLBM_NFIELDS][ny][nx]. */
+pflbm_status pflbm_read_fields(pflbm_domain* d, float* dst, int on_device);
+
+/* The pre-collision populations at the current time level, decoded to
+ * float32: f_out and h_out [9][ny][nx] (either may be NULL). */
+pflbm_status pflbm_read_populations(pflbm_domain* d, float* f_out, float* h_out,
+                                    int on_device);
+
+/* FP64 diagnostics of the current state; geom may be NULL (no pressure
+ * jump).  Synchronises.  Returns EUNSTABLE if any node is non-finite (the
+ * struct is still filled). */
+pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom,
+                               pflbm_diag* out);
+
+/* Checkpoint / resume: the raw state (populations in their storage format,
+ * phi u, step count).  pflbm_state_bytes gives the size of the blob. */
+size_t pflbm_state_bytes(const pflbm_domain* d);
+pflbm_status pflbm_save_state(pflbm_domain* d, void* dst, int on_device);
+pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device);
+
+void pflbm_destroy(pflbm_domain* d);
+
+/* ---- misc ---------------------------------------------------------------- */
+
+const char* pflbm_status_str(pflbm_status s);
+const char* pflbm_last_error(void);
+/* Library version and the device architecture it was compiled for. */
+const char* pflbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFLBM_H */

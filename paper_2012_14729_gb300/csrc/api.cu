@@ -1,0 +1,560 @@
+// Host side of the C ABI declared in include/pflbm.h: workspace layout,
+// parameter checks, launches on the caller's stream, CUDA graph replay,
+// read-back, diagnostics and checkpoints.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "pflbm.h"
+#include "internal.h"
+
+using namespace pflbm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* what, cudaError_t e) {
+  snprintf(g_err, sizeof(g_err), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+void set_msg(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxDiagBlocks = 1024;
+constexpr int kGraphSteps = 64;  // steps captured per graph (even)
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t elem_bytes(int storage) { return storage == kFP32 ? 4 : 2; }
+
+struct Layout {
+  size_t f[2], h[2], h0[2], phiu, fields, partials, red, total;
+};
+
+bool layout_of(int nx, int ny, int storage, Layout* L) {
+  if (nx < 4 || ny < 4 || storage < 0 || storage > 2) return false;
+  const size_t plane = (size_t)(ny + 2) * nx;
+  if (plane * 9 >= (size_t)1 << 31) return false;
+  const size_t n = (size_t)nx * ny;
+  const size_t eb = elem_bytes(storage);
+  const bool split = storage != kFP32;
+  size_t off = 0;
+  for (int b = 0; b < 2; ++b) {
+    L->f[b] = off;
+    off = align_up(off + 9 * plane * eb);
+    L->h[b] = off;
+    off = align_up(off + (split ? 8 : 9) * plane * eb);
+    L->h0[b] = off;
+    off = align_up(off + (split ? plane * 4 : 0));
+  }
+  L->phiu = off;
+  off = align_up(off + 2 * n * 4);
+  L->fields = off;
+  off = align_up(off + (size_t)kNFields * n * 4);
+  L->partials = off;
+  off = align_up(off + (size_t)kMaxDiagBlocks * kNRed * 8);
+  L->red = off;
+  off = align_up(off + kNRed * 8);
+  L->total = off;
+  return true;
+}
+
+}  // namespace
+
+struct pflbm_domain {
+  int nx, ny, wall, storage;
+  cudaStream_t stream;
+  char* ws;
+  Layout lay;
+  int cur;  // buffer holding the current post-collision state
+  long long t;
+  int has_params, has_state;
+  pflbm_params par;
+  Phys phys;
+  int graphs;
+  cudaGraphExec_t gexec;
+  int g_parity;  // buffer parity the captured graph starts from
+};
+
+namespace {
+
+bool is_pow2(double v) {
+  if (!(v > 0) || !isfinite(v)) return false;
+  int e;
+  double m = frexp(v, &e);
+  return m == 0.5;
+}
+
+StepArgs make_args(const pflbm_domain* d, int from) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.L.nx = d->nx;
+  a.L.ny = d->ny;
+  a.L.wall = d->wall;
+  a.L.plane = (d->ny + 2) * d->nx;
+  a.p = d->phys;
+  const int to = 1 - from;
+  a.f_in = d->ws + d->lay.f[from];
+  a.f_out = d->ws + d->lay.f[to];
+  a.h_in = d->ws + d->lay.h[from];
+  a.h_out = d->ws + d->lay.h[to];
+  if (d->storage != kFP32) {
+    a.h0_in = reinterpret_cast<const float*>(d->ws + d->lay.h0[from]);
+    a.h0_out = reinterpret_cast<float*>(d->ws + d->lay.h0[to]);
+  }
+  a.phiu = reinterpret_cast<float*>(d->ws + d->lay.phiu);
+  a.fields = reinterpret_cast<float*>(d->ws + d->lay.fields);
+  return a;
+}
+
+cudaError_t launch_step(const pflbm_domain* d, const StepArgs& a) {
+  const int form = d->par.force;
+  switch (d->storage) {
+    case kFP32: return launch_step_fp32(form, a, d->stream);
+    case kFP16: return launch_step_fp16(form, a, d->stream);
+    default: return launch_step_bf16(form, a, d->stream);
+  }
+}
+
+void drop_graph(pflbm_domain* d) {
+  if (d->gexec) cudaGraphExecDestroy(d->gexec);
+  d->gexec = nullptr;
+}
+
+// One plain step from the current buffer.
+pflbm_status plain_step(pflbm_domain* d) {
+  StepArgs a = make_args(d, d->cur);
+  a.first = d->t == 0;
+  a.macro = 0;
+  cudaError_t e = launch_step(d, a);
+  if (e != cudaSuccess) {
+    set_err("step launch", e);
+    return PFLBM_ECUDA;
+  }
+  d->cur = 1 - d->cur;
+  d->t += 1;
+  return PFLBM_OK;
+}
+
+// Capture kGraphSteps steps (buffers alternating from the current parity).
+pflbm_status capture_graph(pflbm_domain* d) {
+  drop_graph(d);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    set_err("graph capture", e);
+    return PFLBM_ECUDA;
+  }
+  int from = d->cur;
+  for (int k = 0; k < kGraphSteps; ++k) {
+    StepArgs a = make_args(d, from);
+    a.first = 0;
+    a.macro = 0;
+    e = launch_step(d, a);
+    if (e != cudaSuccess) break;
+    from = 1 - from;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(d->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&d->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    d->gexec = nullptr;
+    set_err("graph instantiate", e);
+    return PFLBM_ECUDA;
+  }
+  d->g_parity = d->cur;
+  return PFLBM_OK;
+}
+
+// Macroscopic fields of the current state into the staging buffer.
+pflbm_status stage_fields(pflbm_domain* d) {
+  StepArgs a = make_args(d, d->cur);
+  a.first = d->t == 0;
+  a.macro = 1;
+  cudaError_t e = launch_step(d, a);
+  if (e != cudaSuccess) {
+    set_err("field pass", e);
+    return PFLBM_ECUDA;
+  }
+  return PFLBM_OK;
+}
+
+pflbm_status copy_out(pflbm_domain* d, void* dst, const void* src, size_t bytes, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  d->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    set_err("copy", e);
+    return PFLBM_ECUDA;
+  }
+  return PFLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pflbm_workspace_bytes(int nx, int ny, pflbm_storage storage) {
+  Layout L;
+  if (!layout_of(nx, ny, (int)storage, &L)) return 0;
+  return L.total;
+}
+
+pflbm_status pflbm_create(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y, pflbm_storage storage,
+                          void* dev_workspace, size_t ws_bytes, void* cuda_stream,
+                          pflbm_domain** out) {
+  if (!out) return PFLBM_EINVAL;
+  *out = nullptr;
+  Layout L;
+  if (bc_x != PFLBM_PERIODIC || (bc_y != PFLBM_PERIODIC && bc_y != PFLBM_WALL) ||
+      !layout_of(nx, ny, (int)storage, &L) || !dev_workspace ||
+      ((uintptr_t)dev_workspace % kAlign) != 0) {
+    set_msg("pflbm_create: invalid argument");
+    return PFLBM_EINVAL;
+  }
+  if (ws_bytes < L.total) {
+    set_msg("pflbm_create: workspace too small");
+    return PFLBM_ENOMEM_WS;
+  }
+  pflbm_domain* d = new (std::nothrow) pflbm_domain;
+  if (!d) return PFLBM_EINVAL;
+  memset(d, 0, sizeof(*d));
+  d->nx = nx;
+  d->ny = ny;
+  d->wall = bc_y == PFLBM_WALL;
+  d->storage = (int)storage;
+  d->stream = (cudaStream_t)cuda_stream;
+  d->ws = (char*)dev_workspace;
+  d->lay = L;
+  *out = d;
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_set_params(pflbm_domain* d, const pflbm_params* p) {
+  if (!d || !p) return PFLBM_EINVAL;
+  const bool ok = p->sigma >= 0 && p->W > 0 && p->M > 0 && p->tau_h > 0.5 && p->rho1 > 0 &&
+                  p->rho2 > 0 && p->nu1 > 0 && p->nu2 > 0 && p->eps >= 0 && p->force >= 0 &&
+                  p->force <= 7 && isfinite(p->gx) && isfinite(p->gy) &&
+                  isfinite(p->uw_bottom) && isfinite(p->uw_top) && isfinite(p->sigma) &&
+                  (p->scale_f == 0 || is_pow2(p->scale_f)) &&
+                  (p->scale_h == 0 || is_pow2(p->scale_h));
+  if (!ok) {
+    set_msg("pflbm_set_params: parameter out of range");
+    return PFLBM_EINVAL;
+  }
+  d->par = *p;
+  const double beta = 0.75 * p->sigma / p->W, kappa = 0.375 * p->W * p->sigma;
+  const double th = p->tau_h;
+  Phys& q = d->phys;
+  q.beta4 = (float)(4 * beta);
+  q.kappa = (float)kappa;
+  q.half_sigma = (float)(0.5 * p->sigma);
+  q.eps2 = (float)(p->eps * p->eps);
+  q.rho_mid = (float)(0.5 * (p->rho1 + p->rho2));
+  q.drho_half = (float)(0.5 * (p->rho1 - p->rho2));
+  q.mu_mid = (float)(0.5 * (p->rho1 * p->nu1 + p->rho2 * p->nu2));
+  q.mu_dhalf = (float)(0.5 * (p->rho1 * p->nu1 - p->rho2 * p->nu2));
+  q.gx = (float)p->gx;
+  q.gy = (float)p->gy;
+  q.rho0 = isnan(p->rho0) ? q.rho_mid : (float)p->rho0;  // refined at init
+  q.uwb = (float)p->uw_bottom;
+  q.uwt = (float)p->uw_top;
+  q.inv_tau_h = (float)(1.0 / th);
+  q.hforce = (float)(1.0 - 0.5 / th);
+  q.eta = (float)(p->M / ((th - 0.5) / 3.0));
+  q.acoef = (float)(3.0 * (th * th - th + 1.0 / 6.0) / (th * (th - 0.5)));
+  double s_auto = 1.0;
+  if (p->sigma > 0) s_auto = exp2(round(log2(4.0 / p->sigma)));
+  const double sf = p->scale_f > 0 ? p->scale_f : s_auto;
+  const double sh = p->scale_h > 0 ? p->scale_h : s_auto;
+  q.sf = (float)sf;
+  q.inv_sf = (float)(1.0 / sf);
+  q.sh = (float)sh;
+  q.inv_sh = (float)(1.0 / sh);
+  d->has_params = 1;
+  drop_graph(d);
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
+  if (!d || !phi0) return PFLBM_EINVAL;
+  if (!d->has_params) {
+    set_msg("pflbm_init_phi: parameters not set");
+    return PFLBM_ESTATE;
+  }
+  const size_t n = (size_t)d->nx * d->ny;
+  float* stage = reinterpret_cast<float*>(d->ws + d->lay.fields);
+  cudaError_t e = cudaMemcpyAsync(stage, phi0, n * 4,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  d->stream);
+  // zero both population buffers (ghost rows included)
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->ws, 0, d->lay.phiu, d->stream);
+  d->cur = 0;
+  StepArgs a = make_args(d, 1);  // writes go to buffer 0
+  if (e == cudaSuccess) e = launch_init(d->storage, a, stage, d->stream);
+  if (e != cudaSuccess) {
+    set_err("init", e);
+    return PFLBM_ECUDA;
+  }
+  if (isnan(d->par.rho0)) {
+    // rho is linear in phi, so the mean density is rho(mean phi0)
+    Lattice L = a.L;
+    DiagGeom g = {0, 0, 0, 0, 0};
+    double* red = reinterpret_cast<double*>(d->ws + d->lay.red);
+    double* part = reinterpret_cast<double*>(d->ws + d->lay.partials);
+    // the diagnostics read phi from field slot 0, which holds phi0 here;
+    // the other slots are not needed for the sum of phi
+    e = cudaMemsetAsync(stage + n, 0, (kNFields - 1) * n * 4, d->stream);
+    if (e == cudaSuccess) e = launch_diag(L, stage, g, part, kMaxDiagBlocks, red, d->stream);
+    double h[kNRed];
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, d->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+    if (e != cudaSuccess) {
+      set_err("init mean density", e);
+      return PFLBM_ECUDA;
+    }
+    const double mphi = h[0] / (double)n;
+    d->phys.rho0 = (float)(0.5 * d->par.rho1 * (1 + mphi) + 0.5 * d->par.rho2 * (1 - mphi));
+  }
+  d->t = 0;
+  d->has_state = 1;
+  drop_graph(d);
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable) {
+  if (!d) return PFLBM_EINVAL;
+  if (enable && d->stream == nullptr) {
+    set_msg("pflbm_set_graphs: graphs need a non-default stream");
+    return PFLBM_EINVAL;
+  }
+  d->graphs = enable != 0;
+  if (!d->graphs) drop_graph(d);
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_step(pflbm_domain* d, int nsteps) {
+  if (!d || nsteps < 0) return PFLBM_EINVAL;
+  if (!d->has_state) {
+    set_msg("pflbm_step: no initial state");
+    return PFLBM_ESTATE;
+  }
+  pflbm_status st = PFLBM_OK;
+  int left = nsteps;
+  while (left > 0 && d->t == 0) {
+    if ((st = plain_step(d)) != PFLBM_OK) return st;
+    --left;
+  }
+  if (d->graphs && left >= kGraphSteps) {
+    if (!d->gexec || d->g_parity != d->cur) {
+      if (d->gexec && d->g_parity != d->cur) {
+        if ((st = plain_step(d)) != PFLBM_OK) return st;
+        --left;
+      }
+      if (!d->gexec && (st = capture_graph(d)) != PFLBM_OK) return st;
+    }
+    while (left >= kGraphSteps) {
+      cudaError_t e = cudaGraphLaunch(d->gexec, d->stream);
+      if (e != cudaSuccess) {
+        set_err("graph launch", e);
+        return PFLBM_ECUDA;
+      }
+      d->t += kGraphSteps;  // even: parity unchanged
+      left -= kGraphSteps;
+    }
+  }
+  while (left-- > 0)
+    if ((st = plain_step(d)) != PFLBM_OK) return st;
+  return PFLBM_OK;
+}
+
+long long pflbm_steps_done(const pflbm_domain* d) { return d ? d->t : -1; }
+
+pflbm_status pflbm_read_fields(pflbm_domain* d, float* dst, int on_device) {
+  if (!d || !dst) return PFLBM_EINVAL;
+  if (!d->has_state) return PFLBM_ESTATE;
+  pflbm_status st = stage_fields(d);
+  if (st != PFLBM_OK) return st;
+  const size_t n = (size_t)d->nx * d->ny;
+  return copy_out(d, dst, d->ws + d->lay.fields, (size_t)kNFields * n * 4, on_device);
+}
+
+pflbm_status pflbm_read(pflbm_domain* d, pflbm_field field, float* dst, int on_device) {
+  if (!d || !dst || (int)field < 0 || (int)field >= kNFields) return PFLBM_EINVAL;
+  if (!d->has_state) return PFLBM_ESTATE;
+  pflbm_status st = stage_fields(d);
+  if (st != PFLBM_OK) return st;
+  const size_t n = (size_t)d->nx * d->ny;
+  return copy_out(d, dst, d->ws + d->lay.fields + (size_t)field * n * 4, n * 4, on_device);
+}
+
+pflbm_status pflbm_read_populations(pflbm_domain* d, float* f_out, float* h_out, int on_device) {
+  if (!d || (!f_out && !h_out)) return PFLBM_EINVAL;
+  if (!d->has_state) return PFLBM_ESTATE;
+  const size_t n = (size_t)d->nx * d->ny;
+  // stage through the field buffer (9 fields of n floats fit 9 populations)
+  float* stage = reinterpret_cast<float*>(d->ws + d->lay.fields);
+  StepArgs a = make_args(d, d->cur);
+  float* outs[2] = {f_out, h_out};
+  for (int w = 0; w < 2; ++w) {
+    if (!outs[w]) continue;
+    cudaError_t e = launch_read_pops(d->storage, a, w == 0 ? stage : nullptr,
+                                     w == 1 ? stage : nullptr, d->stream);
+    if (e != cudaSuccess) {
+      set_err("read populations", e);
+      return PFLBM_ECUDA;
+    }
+    pflbm_status st = copy_out(d, outs[w], stage, 9 * n * 4, on_device);
+    if (st != PFLBM_OK) return st;
+  }
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom, pflbm_diag* out) {
+  if (!d || !out) return PFLBM_EINVAL;
+  if (!d->has_state) return PFLBM_ESTATE;
+  pflbm_status st = stage_fields(d);
+  if (st != PFLBM_OK) return st;
+  DiagGeom g = {0, 0, 0, 0, 0};
+  if (geom) g = DiagGeom{geom->xc, geom->yc, geom->r_in, geom->r_out, 1};
+  StepArgs a = make_args(d, d->cur);
+  double* red = reinterpret_cast<double*>(d->ws + d->lay.red);
+  double* part = reinterpret_cast<double*>(d->ws + d->lay.partials);
+  cudaError_t e = launch_diag(a.L, a.fields, g, part, kMaxDiagBlocks, red, d->stream);
+  double h[kNRed];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    set_err("diagnostics", e);
+    return PFLBM_ECUDA;
+  }
+  memset(out, 0, sizeof(*out));
+  out->mass = h[0];
+  out->umax = sqrt(h[1]);
+  out->area1 = h[2];
+  out->R_num = sqrt(h[2] / M_PI);
+  if (g.has_geom && h[9] > 0 && h[11] > 0) {
+    out->p_in = h[8] / h[9];
+    out->p_out = h[10] / h[11];
+    out->dp = out->p_in - out->p_out;
+    out->sigma_num = out->R_num * out->dp;
+  }
+  if (h[2] > 0) {
+    const double cx = h[3] / h[2], cy = h[4] / h[2];
+    out->xc1 = cx;
+    out->yc1 = cy;
+    const double sxx = h[5] / h[2] - cx * cx, syy = h[6] / h[2] - cy * cy;
+    const double sxy = h[7] / h[2] - cx * cy;
+    const double tr = sxx + syy, det = sxx * syy - sxy * sxy;
+    const double disc = sqrt(fmax(tr * tr / 4 - det, 0.0));
+    const double l1 = tr / 2 + disc, l2 = fmax(tr / 2 - disc, 0.0);
+    const double Lx = 4 * sqrt(l1), Bx = 4 * sqrt(l2);
+    out->taylor_D = (Lx + Bx) > 0 ? (Lx - Bx) / (Lx + Bx) : 0.0;
+  }
+  out->nonfinite = h[12];
+  return h[12] > 0 ? PFLBM_EUNSTABLE : PFLBM_OK;
+}
+
+size_t pflbm_state_bytes(const pflbm_domain* d) {
+  if (!d) return 0;
+  // header (step count, magic) + the current population buffers + phi u
+  const Layout& L = d->lay;
+  return 64 + (L.h[0] - L.f[0]) + (L.h0[0] - L.h[0]) + (L.f[1] - L.h0[0]) + (L.fields - L.phiu);
+}
+
+pflbm_status pflbm_save_state(pflbm_domain* d, void* dst, int on_device) {
+  if (!d || !dst) return PFLBM_EINVAL;
+  if (!d->has_state) return PFLBM_ESTATE;
+  const Layout& L = d->lay;
+  long long hdr[8] = {0x70666c626d, d->t, d->nx, d->ny, d->storage, d->wall, 0, 0};
+  char* p = (char*)dst;
+  const cudaMemcpyKind h2x = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  const cudaMemcpyKind d2x = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaMemcpyAsync(p, hdr, sizeof(hdr), h2x, d->stream);
+  p += 64;
+  const int c = d->cur;
+  const size_t sz_f = L.h[0] - L.f[0], sz_h = L.h0[0] - L.h[0], sz_h0 = L.f[1] - L.h0[0];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p, d->ws + L.f[c], sz_f, d2x, d->stream);
+  p += sz_f;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p, d->ws + L.h[c], sz_h, d2x, d->stream);
+  p += sz_h;
+  if (sz_h0 && e == cudaSuccess) e = cudaMemcpyAsync(p, d->ws + L.h0[c], sz_h0, d2x, d->stream);
+  p += sz_h0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p, d->ws + L.phiu, L.fields - L.phiu, d2x, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    set_err("save_state", e);
+    return PFLBM_ECUDA;
+  }
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device) {
+  if (!d || !src) return PFLBM_EINVAL;
+  if (!d->has_params) return PFLBM_ESTATE;
+  const Layout& L = d->lay;
+  long long hdr[8];
+  cudaError_t e = cudaMemcpyAsync(hdr, src, sizeof(hdr),
+                                  on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                                  d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    set_err("load_state", e);
+    return PFLBM_ECUDA;
+  }
+  if (hdr[0] != 0x70666c626d || hdr[2] != d->nx || hdr[3] != d->ny || hdr[4] != d->storage ||
+      hdr[5] != d->wall) {
+    set_msg("pflbm_load_state: state does not match this domain");
+    return PFLBM_EINVAL;
+  }
+  const char* p = (const char*)src + 64;
+  const cudaMemcpyKind x2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t sz_f = L.h[0] - L.f[0], sz_h = L.h0[0] - L.h[0], sz_h0 = L.f[1] - L.h0[0];
+  d->cur = 0;
+  e = cudaMemcpyAsync(d->ws + L.f[0], p, sz_f, x2d, d->stream);
+  p += sz_f;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d->ws + L.h[0], p, sz_h, x2d, d->stream);
+  p += sz_h;
+  if (sz_h0 && e == cudaSuccess) e = cudaMemcpyAsync(d->ws + L.h0[0], p, sz_h0, x2d, d->stream);
+  p += sz_h0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d->ws + L.phiu, p, L.fields - L.phiu, x2d, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    set_err("load_state", e);
+    return PFLBM_ECUDA;
+  }
+  d->t = hdr[1];
+  d->has_state = 1;
+  drop_graph(d);
+  return PFLBM_OK;
+}
+
+void pflbm_destroy(pflbm_domain* d) {
+  if (!d) return;
+  drop_graph(d);
+  delete d;
+}
+
+const char* pflbm_status_str(pflbm_status s) {
+  switch (s) {
+    case PFLBM_OK: return "ok";
+    case PFLBM_EINVAL: return "invalid argument";
+    case PFLBM_ENOMEM_WS: return "workspace too small";
+    case PFLBM_ECUDA: return "CUDA error";
+    case PFLBM_EUNSTABLE: return "non-finite state";
+    case PFLBM_ETIMEOUT: return "device wait timed out";
+    case PFLBM_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* pflbm_last_error(void) { return g_err; }
+
+const char* pflbm_version(void) { return "pflbm 0.1 sm_103a"; }
+
+}  // extern "C"

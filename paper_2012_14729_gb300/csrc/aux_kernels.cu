@@ -1,0 +1,207 @@
+// Initial state, population read-back and FP64 diagnostics of a domain.
+#include "step_kernel.cuh"
+
+namespace pflbm {
+
+// ---------------------------------------------------------------------------
+// initial state (zero velocity, Sec. 5.1): f = f^eq(P = 0, u = 0) = 0 and
+// h = h^eq(phi0, mu0, 0) with mu0 = 4 beta phi0 (phi0^2 - 1) - kappa lap phi0.
+// The pre-collision value h_i(x) is written where the first pull reads it:
+// population plane i at x - c_i (ghost rows for walls, wrapped otherwise).
+// ---------------------------------------------------------------------------
+template <class ST>
+__global__ void k_init(const StepArgs a, const float* __restrict__ phi0) {
+  const Lattice L = a.L;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= L.nx || y >= L.ny) return;
+  auto at = [&](int dx, int dy) {
+    return phi0[map_row(y + dy, L.ny, L.wall) * L.nx + wrap(x + dx, L.nx)];
+  };
+  const float pc = at(0, 0);
+  const float lap = ((at(1, 0) - pc) + (at(-1, 0) - pc) + (at(0, 1) - pc) + (at(0, -1) - pc)) *
+                        (2.0f / 3.0f) +
+                    ((at(1, 1) - pc) + (at(-1, 1) - pc) + (at(1, -1) - pc) + (at(-1, -1) - pc)) *
+                        (1.0f / 6.0f);
+  const float mu = a.p.beta4 * pc * ((pc - 1.0f) * (pc + 1.0f)) - a.p.kappa * lap;
+  const float emu = a.p.eta * mu;
+  // destination of population i: storage position of x - c_i
+  auto dst = [&](int cxi, int cyi) {
+    int sx = x - cxi;
+    if (sx < 0) sx += L.nx;
+    if (sx >= L.nx) sx -= L.nx;
+    int sy = y - cyi;
+    if (!L.wall) {
+      if (sy < 0) sy += L.ny;
+      if (sy >= L.ny) sy -= L.ny;
+    }
+    return (sy + 1) * L.nx + sx;
+  };
+  store_h<ST, 0>(a, dst(0, 0), pc + (qw(0) - 1.0f) * emu);
+  store_h<ST, 1>(a, dst(1, 0), qw(1) * emu);
+  store_h<ST, 2>(a, dst(0, 1), qw(2) * emu);
+  store_h<ST, 3>(a, dst(-1, 0), qw(3) * emu);
+  store_h<ST, 4>(a, dst(0, -1), qw(4) * emu);
+  store_h<ST, 5>(a, dst(1, 1), qw(5) * emu);
+  store_h<ST, 6>(a, dst(-1, 1), qw(6) * emu);
+  store_h<ST, 7>(a, dst(-1, -1), qw(7) * emu);
+  store_h<ST, 8>(a, dst(1, -1), qw(8) * emu);
+  const int n = L.nx * L.ny;
+  a.phiu[y * L.nx + x] = 0.0f;
+  a.phiu[n + y * L.nx + x] = 0.0f;
+}
+
+cudaError_t launch_init(int storage, const StepArgs& a, const float* phi0, cudaStream_t s) {
+  dim3 grid((a.L.nx + 127) / 128, a.L.ny);
+  switch (storage) {
+    case kFP32: k_init<StoreF32><<<grid, 128, 0, s>>>(a, phi0); break;
+    case kFP16: k_init<StoreF16><<<grid, 128, 0, s>>>(a, phi0); break;
+    case kBF16: k_init<StoreBF16><<<grid, 128, 0, s>>>(a, phi0); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// decoded pre-collision populations [9][ny][nx]
+// ---------------------------------------------------------------------------
+template <class ST>
+__global__ void k_read_pops(const StepArgs a, float* f_out, float* h_out) {
+  const Lattice L = a.L;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= L.nx || y >= L.ny) return;
+  const Pull q = pull_idx(L, x, y);
+  const int n = L.nx * L.ny, o = y * L.nx + x;
+  float v[9];
+  if (f_out) {
+    pull_f<ST>(a, q, v);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f_out[i * n + o] = v[i];
+  }
+  if (h_out) {
+    pull_h<ST>(a, q, v);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h_out[i * n + o] = v[i];
+  }
+}
+
+cudaError_t launch_read_pops(int storage, const StepArgs& a, float* f_out, float* h_out,
+                             cudaStream_t s) {
+  dim3 grid((a.L.nx + 127) / 128, a.L.ny);
+  switch (storage) {
+    case kFP32: k_read_pops<StoreF32><<<grid, 128, 0, s>>>(a, f_out, h_out); break;
+    case kFP16: k_read_pops<StoreF16><<<grid, 128, 0, s>>>(a, f_out, h_out); break;
+    case kBF16: k_read_pops<StoreBF16><<<grid, 128, 0, s>>>(a, f_out, h_out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics: per-node terms accumulated in double, reduced by warp
+// shuffles, then across warps in shared memory, one partial row per block;
+// a single-block pass sums the partials in block order (deterministic).
+// Slots: 0 sum phi, 1 max |u|^2, 2 area1 = sum w, 3 sum w x, 4 sum w y,
+// 5 sum w x^2, 6 sum w y^2, 7 sum w x y, 8 sum p_in, 9 n_in, 10 sum p_out,
+// 11 n_out, 12 non-finite count; w = (1 + phi)/2.
+// ---------------------------------------------------------------------------
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
+                                                               const float* __restrict__ fields,
+                                                               const DiagGeom g,
+                                                               double* __restrict__ partials) {
+  const int n = L.nx * L.ny;
+  double acc[13];
+#pragma unroll
+  for (int j = 0; j < 13; ++j) acc[j] = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int y = k / L.nx, x = k - y * L.nx;
+    const double phi = fields[k];
+    const double ux = fields[2 * n + k], uy = fields[3 * n + k];
+    const double ph = fields[6 * n + k];
+    const bool finite = isfinite(phi) && isfinite(ux) && isfinite(uy) && isfinite(ph) &&
+                        isfinite((double)fields[4 * n + k]);
+    if (!finite) {
+      acc[12] += 1.0;
+      continue;
+    }
+    const double w = 0.5 * (1.0 + phi);
+    acc[0] += phi;
+    acc[1] = fmax(acc[1], ux * ux + uy * uy);
+    acc[2] += w;
+    acc[3] += w * x;
+    acc[4] += w * y;
+    acc[5] += w * x * x;
+    acc[6] += w * y * y;
+    acc[7] += w * x * y;
+    if (g.has_geom) {
+      double dx = fabs(x - g.xc), dy = fabs(y - g.yc);
+      dx = fmin(dx, L.nx - dx);
+      dy = fmin(dy, L.ny - dy);
+      const double r = sqrt(dx * dx + dy * dy);
+      if (r <= g.r_in) {
+        acc[8] += ph;
+        acc[9] += 1.0;
+      }
+      if (r >= g.r_out) {
+        acc[10] += ph;
+        acc[11] += 1.0;
+      }
+    }
+  }
+  __shared__ double red[kDiagThreads / 32][13];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 13; ++j) {
+    const double v = (j == 1) ? warp_max(acc[j]) : warp_sum(acc[j]);
+    if (lane == 0) red[wid][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 13) {
+    const int j = threadIdx.x;
+    double v = red[0][j];
+    for (int w = 1; w < kDiagThreads / 32; ++w) v = (j == 1) ? fmax(v, red[w][j]) : v + red[w][j];
+    partials[blockIdx.x * kNRed + j] = v;
+  }
+}
+
+__global__ void k_diag_final(const double* __restrict__ partials, int nblocks,
+                             double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= kNRed) return;
+  double v = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    const double p = (j < 13) ? partials[b * kNRed + j] : 0.0;
+    v = (j == 1) ? fmax(v, p) : v + p;
+  }
+  out[j] = v;
+}
+
+int diag_blocks(int n_nodes, int max_blocks) {
+  int b = (n_nodes + kDiagThreads - 1) / kDiagThreads;
+  if (b > max_blocks) b = max_blocks;
+  return b < 1 ? 1 : b;
+}
+
+cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, double* partials,
+                        int max_blocks, double* red, cudaStream_t s) {
+  const int nb = diag_blocks(L.nx * L.ny, max_blocks);
+  k_diag_partial<<<nb, kDiagThreads, 0, s>>>(L, fields, g, partials);
+  k_diag_final<<<1, 32, 0, s>>>(partials, nb, red);
+  return cudaGetLastError();
+}
+
+}  // namespace pflbm

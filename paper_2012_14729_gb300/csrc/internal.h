@@ -1,0 +1,84 @@
+// Internal declarations of the CUDA library behind include/pflbm.h.
+// Host-side argument blocks of the kernels and the per-storage launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pflbm {
+
+constexpr int kNQ = 9;
+constexpr int kNFields = 9;   // phi, rho, ux, uy, P, mu, p_h, Fx, Fy
+constexpr int kNRed = 16;     // FP64 reduction slots of the diagnostics
+
+enum Storage { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+
+// Physical constants of one domain, precomputed in double on the host and
+// rounded once to float (Sec. 2.1 and Sec. 3 of the paper).
+struct Phys {
+  float beta4;       // 4 beta, beta = 3 sigma / (4 W)
+  float kappa;       // 3 W sigma / 8
+  float half_sigma;  // sigma / 2 (CSF-2)
+  float eps2;        // eps^2 of the CSF normal
+  float rho_mid;     // (rho1 + rho2) / 2:  rho = rho_mid + drho_half phi
+  float drho_half;   // (rho1 - rho2) / 2:  grad rho = drho_half grad phi
+  float mu_mid;      // (rho1 nu1 + rho2 nu2) / 2: dynamic viscosity mid value
+  float mu_dhalf;    // (rho1 nu1 - rho2 nu2) / 2
+  float gx, gy, rho0;
+  float uwb, uwt;    // x-velocity of the bottom / top wall
+  float inv_tau_h;   // 1 / tau_h
+  float hforce;      // 1 - 1 / (2 tau_h)
+  float eta;         // M / (cs^2 (tau_h - 1/2))
+  float acoef;       // 3 tau2 / (tau_h tau1)
+  float sf, inv_sf;  // 16-bit storage scales of f
+  float sh, inv_sh;  // and of h_1..h_8
+};
+
+struct Lattice {
+  int nx, ny;
+  int wall;          // 1: half-way bounce-back walls at y = -1/2, ny - 1/2
+  int plane;         // elements per population plane: (ny + 2) * nx
+};
+
+// Arguments of one fused step (or macroscopic read) over one domain.
+struct StepArgs {
+  Lattice L;
+  Phys p;
+  const void* f_in;   // post-collision populations of the previous step
+  void* f_out;        // written by this step
+  const void* h_in;   // FP32: 9 planes; 16-bit: planes of h_1..h_8
+  void* h_out;
+  const float* h0_in; // 16-bit storage only: h_0 in float32
+  float* h0_out;
+  float* phiu;        // [2][ny][nx]: in (phi u)^{t-1}, out (phi u)^t
+  float* fields;      // macro mode: [kNFields][ny][nx]
+  int first;          // first step of a run: d_t(phi u) = 0
+  int macro;          // 1: write fields instead of colliding
+};
+
+// Tile of the fused step kernel.
+constexpr int kTX = 32;
+constexpr int kTY = 16;
+constexpr int kThreads = 256;
+
+cudaError_t launch_step_fp32(int form, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp16(int form, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_bf16(int form, const StepArgs& a, cudaStream_t s);
+
+// Initial state from phi0 (device, [ny][nx]).
+cudaError_t launch_init(int storage, const StepArgs& a, const float* phi0, cudaStream_t s);
+// Decoded pre-collision populations (either output may be null).
+cudaError_t launch_read_pops(int storage, const StepArgs& a, float* f_out, float* h_out,
+                             cudaStream_t s);
+
+struct DiagGeom {
+  double xc, yc, r_in, r_out;
+  int has_geom;
+};
+// FP64 reductions of the staged fields into red[kNRed] (partials in scratch).
+cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, double* partials,
+                        int max_blocks, double* red, cudaStream_t s);
+int diag_blocks(int n_nodes, int max_blocks);
+
+}  // namespace pflbm
