@@ -106,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -212,6 +212,24 @@ def run_ours(args, case):
     stream = dom.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.__enter__()
+    # warm-up: at least `warmup` steps and at least ~1 s of load, so that the
+    # clock sampler (50 ms period) sees the GPU under load around the timed
+    # region, which itself can be shorter than one sample
+    t_w = time.perf_counter()
+    k = 0
+    with torch.cuda.stream(stream):
+        while time.perf_counter() - t_w < args.load_seconds:
+            flush.zero_()
+            dom.step(1)
+            k += 1
+            if k % 64 == 0:
+                stream.synchronize()
+    stream.synchronize()
+    # restart the run from phi0 so that the timed steps follow the workload's
+    # initial condition (the warm-up load above can run for thousands of steps)
+    dom.init_phi(case.phi0.astype(np.float32))
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
@@ -224,15 +242,16 @@ def run_ours(args, case):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        with torch.cuda.stream(stream):
-            for e0, e1 in evs:
-                flush.zero_()          # cold L2 for every timed step
-                e0.record(stream)
-                dom.step(1)            # one fused kernel launch
-                e1.record(stream)
-        stream.synchronize()
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            flush.zero_()          # cold L2 for every timed step
+            e0.record(stream)
+            dom.step(1)            # one fused kernel launch
+            e1.record(stream)
+    stream.synchronize()
     torch.cuda.synchronize()
+    time.sleep(0.15)  # one more clock sample after the timed region
+    clk.__exit__(None, None, None)
     per_step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     t_ms = sum(per_step_ms)
     if ws > 1:
@@ -323,6 +342,7 @@ def main():
     ap.add_argument("--form", default="STF1")
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp16", "bf16"))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -8,6 +8,8 @@
 #include <new>
 
 #include "pflbm.h"
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 
 using namespace pflbm;
@@ -30,7 +32,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 size_t elem_bytes(int storage) { return storage == kFP32 ? 4 : 2; }
 
 struct Layout {
-  size_t f[2], h[2], h0[2], phiu, fields, partials, red, total;
+  size_t f[2], h[2], h0[2], phiu, fields, partials, red, err, total;
 };
 
 bool layout_of(int nx, int ny, int storage, Layout* L) {
@@ -57,6 +59,8 @@ bool layout_of(int nx, int ny, int storage, Layout* L) {
   off = align_up(off + (size_t)kMaxDiagBlocks * kNRed * 8);
   L->red = off;
   off = align_up(off + kNRed * 8);
+  L->err = off;
+  off = align_up(off + 4);
   L->total = off;
   return true;
 }
@@ -73,6 +77,9 @@ struct pflbm_domain {
   int has_params, has_state;
   pflbm_params par;
   Phys phys;
+  // TMA descriptors of the input population arrays of each buffer
+  CUtensorMap tm_f[2], tm_h[2], tm_h0[2];
+  int use_tma;
   int graphs;
   cudaGraphExec_t gexec;
   int g_parity;  // buffer parity the captured graph starts from
@@ -106,7 +113,69 @@ StepArgs make_args(const pflbm_domain* d, int from) {
   }
   a.phiu = reinterpret_cast<float*>(d->ws + d->lay.phiu);
   a.fields = reinterpret_cast<float*>(d->ws + d->lay.fields);
+  a.err = reinterpret_cast<int*>(d->ws + d->lay.err);
+  a.use_tma = d->use_tma;
+  if (d->use_tma) {
+    a.tm_f = d->tm_f[from];
+    a.tm_h = d->tm_h[from];
+    a.tm_h0 = d->tm_h0[from];
+  }
   return a;
+}
+
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// A [planes * rows][nx] array as a 2-D tensor with boxes of box_rows rows of
+// box_w(elem) columns.
+bool encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int elem, int nx,
+                long long rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)nx * elem};
+  cuuint32_t box[2] = {(cuuint32_t)box_w(elem), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of both buffers; TMA is used only when the row pitch is a
+// multiple of 16 bytes and the grid is wide enough for interior tiles.
+void build_maps(pflbm_domain* d) {
+  d->use_tma = 0;
+  const int eb = (int)elem_bytes(d->storage);
+  if ((d->nx * eb) % 16 != 0) return;
+  const CUtensorMapDataType dt = d->storage == kFP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : d->storage == kFP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const long long rows = d->ny + 2;
+  const bool split = d->storage != kFP32;
+  bool ok = true;
+  for (int b = 0; b < 2 && ok; ++b) {
+    ok = encode_map(&d->tm_f[b], d->ws + d->lay.f[b], dt, eb, d->nx, 9 * rows, kBoxRowsF) &&
+         encode_map(&d->tm_h[b], d->ws + d->lay.h[b], dt, eb, d->nx, (split ? 8 : 9) * rows,
+                    kBoxRowsH);
+    if (ok && split)
+      ok = encode_map(&d->tm_h0[b], d->ws + d->lay.h0[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                      d->nx, rows, kBoxRowsH);
+    if (ok && !split) d->tm_h0[b] = d->tm_h[b];
+  }
+  d->use_tma = ok ? 1 : 0;
 }
 
 cudaError_t launch_step(const pflbm_domain* d, const StepArgs& a) {
@@ -321,6 +390,12 @@ pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
     const double mphi = h[0] / (double)n;
     d->phys.rho0 = (float)(0.5 * d->par.rho1 * (1 + mphi) + 0.5 * d->par.rho2 * (1 - mphi));
   }
+  e = cudaMemsetAsync(d->ws + d->lay.err, 0, 4, d->stream);
+  if (e != cudaSuccess) {
+    set_err("init", e);
+    return PFLBM_ECUDA;
+  }
+  build_maps(d);
   d->t = 0;
   d->has_state = 1;
   drop_graph(d);
@@ -427,7 +502,10 @@ pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom, pfl
   double* part = reinterpret_cast<double*>(d->ws + d->lay.partials);
   cudaError_t e = launch_diag(a.L, a.fields, g, part, kMaxDiagBlocks, red, d->stream);
   double h[kNRed];
+  int err_word = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&err_word, d->ws + d->lay.err, 4, cudaMemcpyDeviceToHost, d->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
   if (e != cudaSuccess) {
     set_err("diagnostics", e);
@@ -457,6 +535,10 @@ pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom, pfl
     out->taylor_D = (Lx + Bx) > 0 ? (Lx - Bx) / (Lx + Bx) : 0.0;
   }
   out->nonfinite = h[12];
+  if (err_word) {
+    set_msg("a bounded device wait expired during a step");
+    return PFLBM_ETIMEOUT;
+  }
   return h[12] > 0 ? PFLBM_EUNSTABLE : PFLBM_OK;
 }
 
@@ -528,6 +610,12 @@ pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device) {
     set_err("load_state", e);
     return PFLBM_ECUDA;
   }
+  e = cudaMemsetAsync(d->ws + L.err, 0, 4, d->stream);
+  if (e != cudaSuccess) {
+    set_err("load_state", e);
+    return PFLBM_ECUDA;
+  }
+  build_maps(d);
   d->t = hdr[1];
   d->has_state = 1;
   drop_graph(d);

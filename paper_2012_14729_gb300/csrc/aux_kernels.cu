@@ -1,5 +1,5 @@
 // Initial state, population read-back and FP64 diagnostics of a domain.
-#include "step_kernel.cuh"
+#include "lattice.cuh"
 
 namespace pflbm {
 

@@ -2,6 +2,7 @@
 // Host-side argument blocks of the kernels and the per-storage launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -41,8 +42,15 @@ struct Lattice {
   int plane;         // elements per population plane: (ny + 2) * nx
 };
 
-// Arguments of one fused step (or macroscopic read) over one domain.
+// Arguments of one fused step (or macroscopic read) over one domain.  The
+// tensor maps describe the input population arrays as 2-D tensors of
+// nplanes * (ny + 2) rows of nx elements, for TMA box loads.
 struct StepArgs {
+  CUtensorMap tm_f;   // f_in (9 planes)
+  CUtensorMap tm_h;   // h_in (9 planes, or 8 planes h_1..h_8 for 16-bit storage)
+  CUtensorMap tm_h0;  // h0_in (16-bit storage only)
+  int use_tma;        // tensor maps valid and row pitch 16-byte aligned
+  int* err;           // device error word: bit 0 = a bounded wait expired
   Lattice L;
   Phys p;
   const void* f_in;   // post-collision populations of the previous step
@@ -61,6 +69,16 @@ struct StepArgs {
 constexpr int kTX = 32;
 constexpr int kTY = 16;
 constexpr int kThreads = 256;
+// Spin limit of the kernel's mbarrier waits (each try_wait suspends for a
+// hardware-bounded time); past it the kernel flags err and returns.
+constexpr long long kWaitLimit = 1ll << 22;
+
+// Box geometry of the TMA loads for a storage element size: columns
+// [x0 - xpad, x0 + kTX + xpad) so that the start column is 16-byte aligned.
+__host__ __device__ constexpr int box_xpad(int elem_bytes) { return 16 / elem_bytes; }
+__host__ __device__ constexpr int box_w(int elem_bytes) { return kTX + 2 * box_xpad(elem_bytes); }
+constexpr int kBoxRowsH = kTY + 6;  // phi is needed on the tile + 3 ring
+constexpr int kBoxRowsF = kTY + 2;  // f on the tile + 1 ring
 
 cudaError_t launch_step_fp32(int form, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp16(int form, const StepArgs& a, cudaStream_t s);

@@ -1,0 +1,212 @@
+// Device helpers shared by the step kernel and the auxiliary kernels: the
+// D2Q9 lattice (Sec. 3 of Zhang, Liang & Guo, arXiv 2012.14729), population
+// storage formats, pull indexing with ghost rows for half-way bounce-back
+// walls (Sec. 4), and the isotropic central-scheme stencils (Eqs. ICS-1st,
+// ICS-sec) on shared-memory arrays.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace pflbm {
+
+// ---------------------------------------------------------------------------
+// D2Q9 lattice: c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
+// (-1,-1),(1,-1), weights 4/9, 1/9, 1/36 (Sec. 3)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int qcx(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int qcy(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr float qw(int i) {
+  return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr int qopp(int i) {
+  return i == 0 ? 0 : (i < 5 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+
+enum Form { kSTF1 = 0, kSTF2, kCPF1, kCPF2, kPF1, kPF2, kCSF1, kCSF2 };
+
+// Number of form-specific level-1 fields kept in shared memory.
+template <int FORM>
+__host__ __device__ constexpr int extra_fields() {
+  return (FORM == kSTF1 || FORM == kSTF2) ? 3 : ((FORM == kCSF1 || FORM == kCSF2) ? 2 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// storage formats
+// ---------------------------------------------------------------------------
+struct StoreF32 {
+  static constexpr bool kSplitH0 = false;
+  using T = float;
+  __device__ static __forceinline__ float dec(T v, float w_inv_scale) { return v; }
+  __device__ static __forceinline__ T enc(float v, float scale_over_w) { return v; }
+};
+struct StoreF16 {
+  static constexpr bool kSplitH0 = true;
+  using T = __half;
+  __device__ static __forceinline__ float dec(T v, float w_inv_scale) {
+    return __half2float(v) * w_inv_scale;
+  }
+  __device__ static __forceinline__ T enc(float v, float scale_over_w) {
+    return __float2half_rn(v * scale_over_w);
+  }
+};
+struct StoreBF16 {
+  static constexpr bool kSplitH0 = true;
+  using T = __nv_bfloat16;
+  __device__ static __forceinline__ float dec(T v, float w_inv_scale) {
+    return __bfloat162float(v) * w_inv_scale;
+  }
+  __device__ static __forceinline__ T enc(float v, float scale_over_w) {
+    return __float2bfloat16_rn(v * scale_over_w);
+  }
+};
+
+// f_i, population i at storage index idx
+template <class ST, int I>
+__device__ __forceinline__ float load_f(const StepArgs& a, int idx) {
+  using T = typename ST::T;
+  const T* base = reinterpret_cast<const T*>(a.f_in) + (size_t)I * a.L.plane;
+  if constexpr (ST::kSplitH0) return ST::dec(__ldg(base + idx), qw(I) * a.p.inv_sf);
+  else return __ldg(base + idx);
+}
+template <class ST, int I>
+__device__ __forceinline__ float load_h(const StepArgs& a, int idx) {
+  using T = typename ST::T;
+  if constexpr (ST::kSplitH0) {
+    if constexpr (I == 0) return __ldg(a.h0_in + idx);
+    else {
+      const T* base = reinterpret_cast<const T*>(a.h_in) + (size_t)(I - 1) * a.L.plane;
+      return ST::dec(__ldg(base + idx), qw(I) * a.p.inv_sh);
+    }
+  } else {
+    const T* base = reinterpret_cast<const T*>(a.h_in) + (size_t)I * a.L.plane;
+    return __ldg(base + idx);
+  }
+}
+template <class ST, int I>
+__device__ __forceinline__ void store_f(const StepArgs& a, int idx, float v) {
+  using T = typename ST::T;
+  T* base = reinterpret_cast<T*>(a.f_out) + (size_t)I * a.L.plane;
+  if constexpr (ST::kSplitH0) base[idx] = ST::enc(v, a.p.sf * (1.0f / qw(I)));
+  else base[idx] = v;
+}
+template <class ST, int I>
+__device__ __forceinline__ void store_h(const StepArgs& a, int idx, float v) {
+  using T = typename ST::T;
+  if constexpr (ST::kSplitH0) {
+    if constexpr (I == 0) a.h0_out[idx] = v;
+    else {
+      T* base = reinterpret_cast<T*>(a.h_out) + (size_t)(I - 1) * a.L.plane;
+      base[idx] = ST::enc(v, a.p.sh * (1.0f / qw(I)));
+    }
+  } else {
+    T* base = reinterpret_cast<T*>(a.h_out) + (size_t)I * a.L.plane;
+    base[idx] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// index helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap(int v, int n) {
+  if (v >= 0 && v < n) return v;
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+// Row of a scalar-field node: periodic wrap, or mirror about the walls.
+__device__ __forceinline__ int map_row(int y, int ny, int wall) {
+  if (y >= 0 && y < ny) return y;
+  if (!wall) return wrap(y, ny);
+  while (y < 0 || y >= ny) y = (y < 0) ? -y - 1 : 2 * ny - 1 - y;
+  return y;
+}
+
+// Storage indices of the 9 pulled populations of node (x, y), 0 <= x < nx,
+// 0 <= y < ny: population i comes from (x - cx_i, y - cy_i); storage row is
+// domain row + 1 (ghost rows 0 and ny + 1 hold bounced populations).
+struct Pull {
+  int i[9];
+};
+__device__ __forceinline__ Pull pull_idx(const Lattice& L, int x, int y) {
+  int xm = x + 1, xp = x - 1;  // source columns for cx = -1 and cx = +1
+  if (xm >= L.nx) xm -= L.nx;
+  if (xp < 0) xp += L.nx;
+  int ym = y + 1, yp = y - 1;  // source rows for cy = -1 and cy = +1
+  if (!L.wall) {
+    if (ym >= L.ny) ym -= L.ny;
+    if (yp < 0) yp += L.ny;
+  }
+  const int r0 = (y + 1) * L.nx, rm = (ym + 1) * L.nx, rp = (yp + 1) * L.nx;
+  Pull p;
+  p.i[0] = r0 + x;
+  p.i[1] = r0 + xp;
+  p.i[2] = rp + x;
+  p.i[3] = r0 + xm;
+  p.i[4] = rm + x;
+  p.i[5] = rp + xp;
+  p.i[6] = rp + xm;
+  p.i[7] = rm + xm;
+  p.i[8] = rm + xp;
+  return p;
+}
+
+template <class ST>
+__device__ __forceinline__ float pull_phi(const StepArgs& a, const Pull& q) {
+  // summed in direction order 0..8
+  float s = load_h<ST, 0>(a, q.i[0]);
+  s += load_h<ST, 1>(a, q.i[1]);
+  s += load_h<ST, 2>(a, q.i[2]);
+  s += load_h<ST, 3>(a, q.i[3]);
+  s += load_h<ST, 4>(a, q.i[4]);
+  s += load_h<ST, 5>(a, q.i[5]);
+  s += load_h<ST, 6>(a, q.i[6]);
+  s += load_h<ST, 7>(a, q.i[7]);
+  s += load_h<ST, 8>(a, q.i[8]);
+  return s;
+}
+
+template <class ST>
+__device__ __forceinline__ void pull_f(const StepArgs& a, const Pull& q, float* f) {
+  f[0] = load_f<ST, 0>(a, q.i[0]);
+  f[1] = load_f<ST, 1>(a, q.i[1]);
+  f[2] = load_f<ST, 2>(a, q.i[2]);
+  f[3] = load_f<ST, 3>(a, q.i[3]);
+  f[4] = load_f<ST, 4>(a, q.i[4]);
+  f[5] = load_f<ST, 5>(a, q.i[5]);
+  f[6] = load_f<ST, 6>(a, q.i[6]);
+  f[7] = load_f<ST, 7>(a, q.i[7]);
+  f[8] = load_f<ST, 8>(a, q.i[8]);
+}
+template <class ST>
+__device__ __forceinline__ void pull_h(const StepArgs& a, const Pull& q, float* h) {
+  h[0] = load_h<ST, 0>(a, q.i[0]);
+  h[1] = load_h<ST, 1>(a, q.i[1]);
+  h[2] = load_h<ST, 2>(a, q.i[2]);
+  h[3] = load_h<ST, 3>(a, q.i[3]);
+  h[4] = load_h<ST, 4>(a, q.i[4]);
+  h[5] = load_h<ST, 5>(a, q.i[5]);
+  h[6] = load_h<ST, 6>(a, q.i[6]);
+  h[7] = load_h<ST, 7>(a, q.i[7]);
+  h[8] = load_h<ST, 8>(a, q.i[8]);
+}
+
+// Central-scheme derivatives (Eq. ICS-1st) of a shared-memory field at
+// element c with row stride S: d/dx = 3 sum_i w_i c_ix a(x + c_i).
+template <int S>
+__device__ __forceinline__ float ics_dx(const float* a, int c) {
+  return (a[c + 1] - a[c - 1]) * (1.0f / 3.0f) +
+         ((a[c + S + 1] - a[c + S - 1]) + (a[c - S + 1] - a[c - S - 1])) * (1.0f / 12.0f);
+}
+template <int S>
+__device__ __forceinline__ float ics_dy(const float* a, int c) {
+  return (a[c + S] - a[c - S]) * (1.0f / 3.0f) +
+         ((a[c + S + 1] - a[c - S + 1]) + (a[c + S - 1] - a[c - S - 1])) * (1.0f / 12.0f);
+}
+
+}  // namespace pflbm

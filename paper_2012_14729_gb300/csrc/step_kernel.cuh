@@ -1,19 +1,30 @@
 // Fused coupled step of the phase-field lattice Boltzmann method (Sec. 3 of
 // Zhang, Liang & Guo, arXiv 2012.14729) for sm_103a.
 //
-// One CTA owns a kTX x kTY tile of nodes and runs the whole time step for it
-// in four passes over shared memory, recomputing what its neighbours need on
-// a halo instead of exchanging it through HBM:
-//   pass 1  phi = sum_i h_i on the tile + 3 ring (pull of h, Eq. mac)
+// One CTA owns a kTX x kTY tile of nodes and runs the whole time step for it.
+//
+// Staging.  The post-collision populations of the previous step are brought
+// into shared memory as one 2-D box per population plane: h planes on the
+// tile + 3 ring (rows) and f planes on the tile + 1 ring, each box shifted by
+// -c_i in y so that its rows hold the pulled values; in x every box spans the
+// same 16-byte aligned column range and the -c_ix shift is applied when the
+// box is read.  Interior tiles issue the 18 boxes as TMA tensor loads
+// (cp.async.bulk.tensor) completing on one mbarrier; tiles whose boxes wrap
+// around the periodic seam or reach the wall ghost rows fill the same boxes
+// with plain loads.
+//
+// Passes over shared memory, recomputing the halo a tile's nodes need
+// instead of exchanging it through HBM:
+//   pass 1  phi = sum_i h_i on the tile + 3 ring (Eq. mac)
 //   pass 2  grad phi, lap phi (Eqs. ICS-1st, ICS-sec), mu (Eq.
 //           chemical_potential) and the form's level-1 fields on tile + 2
 //   pass 3  interfacial + gravity force (Sec. 2.2), rho, u and phi u on
-//           tile + 1 (pull of f, Eq. mac)
+//           tile + 1 (Eq. mac)
 //   pass 4  on the tile: P, div(phi u), d_t(phi u), BGK collision of f and h
 //           with F_i and H_i (Eqs. fh, P_LBM, CH_LB_force), store of the
 //           post-collision populations; streaming is the next step's pull.
 // HBM traffic per node and step is the algorithmic state: 18 populations read
-// and written plus (phi u) read and written; halo re-reads hit L1/L2.
+// and written plus (phi u) read and written; halo re-reads hit L2.
 //
 // Walls (Sec. 4, half-way bounce-back): populations are stored with one
 // ghost row below and above the domain.  A node next to a wall writes the
@@ -23,242 +34,234 @@
 // mirrored node.
 #pragma once
 
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "internal.h"
+#include "lattice.cuh"
 
 namespace pflbm {
 
 // ---------------------------------------------------------------------------
-// D2Q9 lattice: c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
-// (-1,-1),(1,-1), weights 4/9, 1/9, 1/36 (Sec. 3)
+// TMA and mbarrier (inline PTX)
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int qcx(int i) {
-  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-__host__ __device__ constexpr int qcy(int i) {
-  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
 }
-__host__ __device__ constexpr float qw(int i) {
-  return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__host__ __device__ constexpr int qopp(int i) {
-  return i == 0 ? 0 : (i < 5 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
 }
-
-enum Form { kSTF1 = 0, kSTF2, kCPF1, kCPF2, kPF1, kPF2, kCSF1, kCSF2 };
-
-// Number of form-specific level-1 fields kept in shared memory.
-template <int FORM>
-__host__ __device__ constexpr int extra_fields() {
-  return (FORM == kSTF1 || FORM == kSTF2) ? 3 : ((FORM == kCSF1 || FORM == kCSF2) ? 2 : 0);
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// 2-D tensor tile load global -> shared, completion counted on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // ---------------------------------------------------------------------------
-// storage formats
+// shared-memory geometry of one CTA
 // ---------------------------------------------------------------------------
-struct StoreF32 {
-  static constexpr bool kSplitH0 = false;
-  using T = float;
-  __device__ static __forceinline__ float dec(T v, float w_inv_scale) { return v; }
-  __device__ static __forceinline__ T enc(float v, float scale_over_w) { return v; }
-};
-struct StoreF16 {
-  static constexpr bool kSplitH0 = true;
-  using T = __half;
-  __device__ static __forceinline__ float dec(T v, float w_inv_scale) {
-    return __half2float(v) * w_inv_scale;
-  }
-  __device__ static __forceinline__ T enc(float v, float scale_over_w) {
-    return __float2half_rn(v * scale_over_w);
-  }
-};
-struct StoreBF16 {
-  static constexpr bool kSplitH0 = true;
-  using T = __nv_bfloat16;
-  __device__ static __forceinline__ float dec(T v, float w_inv_scale) {
-    return __bfloat162float(v) * w_inv_scale;
-  }
-  __device__ static __forceinline__ T enc(float v, float scale_over_w) {
-    return __float2bfloat16_rn(v * scale_over_w);
-  }
-};
+__host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; }
 
-// f_i, population i at storage index idx
-template <class ST, int I>
-__device__ __forceinline__ float load_f(const StepArgs& a, int idx) {
+template <class ST, int FORM>
+struct Smem {
   using T = typename ST::T;
-  const T* base = reinterpret_cast<const T*>(a.f_in) + (size_t)I * a.L.plane;
-  if constexpr (ST::kSplitH0) return ST::dec(__ldg(base + idx), qw(I) * a.p.inv_sf);
-  else return __ldg(base + idx);
-}
-template <class ST, int I>
-__device__ __forceinline__ float load_h(const StepArgs& a, int idx) {
-  using T = typename ST::T;
-  if constexpr (ST::kSplitH0) {
-    if constexpr (I == 0) return __ldg(a.h0_in + idx);
-    else {
-      const T* base = reinterpret_cast<const T*>(a.h_in) + (size_t)(I - 1) * a.L.plane;
-      return ST::dec(__ldg(base + idx), qw(I) * a.p.inv_sh);
-    }
+  static constexpr int EB = sizeof(T);
+  static constexpr int XPAD = box_xpad(EB);
+  static constexpr int PW = box_w(EB);
+  static constexpr int RH = kBoxRowsH, RF = kBoxRowsF;
+  // boxes: h planes (h_0 in float32 when the storage is split), f planes
+  static constexpr int HB0 = pad128(RH * PW * (ST::kSplitH0 ? 4 : EB));
+  static constexpr int HB = pad128(RH * PW * EB);
+  static constexpr int FB = pad128(RF * PW * EB);
+  static constexpr int B3X = kTX + 6, B3Y = kTY + 6;
+  static constexpr int B2X = kTX + 4, B2Y = kTY + 4;
+  static constexpr int B1X = kTX + 2, B1Y = kTY + 2;
+  static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
+  static constexpr int NE = extra_fields<FORM>();
+  static constexpr int OFF_BAR = 0;
+  static constexpr int OFF_H = 128;
+  static constexpr int OFF_F = OFF_H + HB0 + 8 * HB;
+  static constexpr int OFF_PHI = OFF_F + 9 * FB;
+  static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
+  static constexpr int OFF_S1 = OFF_S2 + pad128((4 + NE) * N2 * 4);
+  static constexpr int BYTES = OFF_S1 + pad128(6 * N1 * 4);
+  static constexpr int TMA_BYTES = HB0 + 8 * HB + 9 * FB;  // counted per box, padded
+  static constexpr int TMA_TX = RH * PW * (ST::kSplitH0 ? 4 : EB) + 8 * RH * PW * EB +
+                                9 * RF * PW * EB;  // bytes the 18 loads deliver
+
+  __device__ static int h_off(int i) { return OFF_H + (i == 0 ? 0 : HB0 + (i - 1) * HB); }
+  __device__ static int f_off(int i) { return OFF_F + i * FB; }
+};
+
+// population i of a box at (row, col), decoded to float
+template <class ST, int I, class G>
+__device__ __forceinline__ float box_h(const unsigned char* sm, int r, int c, const Phys& P) {
+  if constexpr (ST::kSplitH0 && I == 0) {
+    return reinterpret_cast<const float*>(sm + G::h_off(0))[r * G::PW + c];
   } else {
-    const T* base = reinterpret_cast<const T*>(a.h_in) + (size_t)I * a.L.plane;
-    return __ldg(base + idx);
+    const typename ST::T v = reinterpret_cast<const typename ST::T*>(sm + G::h_off(I))[r * G::PW + c];
+    return ST::dec(v, qw(I) * P.inv_sh);
   }
 }
-template <class ST, int I>
-__device__ __forceinline__ void store_f(const StepArgs& a, int idx, float v) {
-  using T = typename ST::T;
-  T* base = reinterpret_cast<T*>(a.f_out) + (size_t)I * a.L.plane;
-  if constexpr (ST::kSplitH0) base[idx] = ST::enc(v, a.p.sf * (1.0f / qw(I)));
-  else base[idx] = v;
+template <class ST, int I, class G>
+__device__ __forceinline__ float box_f(const unsigned char* sm, int r, int c, const Phys& P) {
+  const typename ST::T v = reinterpret_cast<const typename ST::T*>(sm + G::f_off(I))[r * G::PW + c];
+  return ST::dec(v, qw(I) * P.inv_sf);
 }
-template <class ST, int I>
-__device__ __forceinline__ void store_h(const StepArgs& a, int idx, float v) {
+
+// Fill the boxes with plain loads (tiles at the periodic seam or the walls).
+// Box row r of plane i holds storage row (node row - c_iy) + 1 of the rows
+// the tile needs; rows the tile never pulls (beyond a wall) are zero.
+template <class ST, class G>
+__device__ void fill_boxes_plain(const StepArgs& a, unsigned char* sm, int x0, int y0) {
   using T = typename ST::T;
-  if constexpr (ST::kSplitH0) {
-    if constexpr (I == 0) a.h0_out[idx] = v;
-    else {
-      T* base = reinterpret_cast<T*>(a.h_out) + (size_t)(I - 1) * a.L.plane;
-      base[idx] = ST::enc(v, a.p.sh * (1.0f / qw(I)));
+  const Lattice& L = a.L;
+  auto srow = [&](int yy) -> int {  // storage row of source domain row yy, or -1
+    if (L.wall) return (yy >= -1 && yy <= L.ny) ? yy + 1 : -1;
+    return wrap(yy, L.ny) + 1;
+  };
+  for (int e = threadIdx.x; e < G::RH * G::PW; e += kThreads) {
+    const int r = e / G::PW, c = e - r * G::PW;
+    const int gx = wrap(x0 - G::XPAD + c, L.nx);
+    const int yn = y0 - 3 + r;  // node row
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int sr = srow(yn - qcy(i));
+      if (ST::kSplitH0 && i == 0) {
+        reinterpret_cast<float*>(sm + G::h_off(0))[e] = sr >= 0 ? a.h0_in[sr * L.nx + gx] : 0.0f;
+      } else {
+        const int pl = ST::kSplitH0 ? i - 1 : i;
+        const T* src = reinterpret_cast<const T*>(a.h_in) + (size_t)pl * L.plane;
+        reinterpret_cast<T*>(sm + G::h_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
+      }
     }
-  } else {
-    T* base = reinterpret_cast<T*>(a.h_out) + (size_t)I * a.L.plane;
-    base[idx] = v;
   }
-}
-
-// ---------------------------------------------------------------------------
-// index helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int wrap(int v, int n) {
-  if (v >= 0 && v < n) return v;
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-// Row of a scalar-field node: periodic wrap, or mirror about the walls.
-__device__ __forceinline__ int map_row(int y, int ny, int wall) {
-  if (y >= 0 && y < ny) return y;
-  if (!wall) return wrap(y, ny);
-  while (y < 0 || y >= ny) y = (y < 0) ? -y - 1 : 2 * ny - 1 - y;
-  return y;
-}
-
-// Storage indices of the 9 pulled populations of node (x, y), 0 <= x < nx,
-// 0 <= y < ny: population i comes from (x - cx_i, y - cy_i); storage row is
-// domain row + 1 (ghost rows 0 and ny + 1 hold bounced populations).
-struct Pull {
-  int i[9];
-};
-__device__ __forceinline__ Pull pull_idx(const Lattice& L, int x, int y) {
-  int xm = x + 1, xp = x - 1;  // source columns for cx = -1 and cx = +1
-  if (xm >= L.nx) xm -= L.nx;
-  if (xp < 0) xp += L.nx;
-  int ym = y + 1, yp = y - 1;  // source rows for cy = -1 and cy = +1
-  if (!L.wall) {
-    if (ym >= L.ny) ym -= L.ny;
-    if (yp < 0) yp += L.ny;
+  for (int e = threadIdx.x; e < G::RF * G::PW; e += kThreads) {
+    const int r = e / G::PW, c = e - r * G::PW;
+    const int gx = wrap(x0 - G::XPAD + c, L.nx);
+    const int yn = y0 - 1 + r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int sr = srow(yn - qcy(i));
+      const T* src = reinterpret_cast<const T*>(a.f_in) + (size_t)i * L.plane;
+      reinterpret_cast<T*>(sm + G::f_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
+    }
   }
-  const int r0 = (y + 1) * L.nx, rm = (ym + 1) * L.nx, rp = (yp + 1) * L.nx;
-  Pull p;
-  p.i[0] = r0 + x;
-  p.i[1] = r0 + xp;
-  p.i[2] = rp + x;
-  p.i[3] = r0 + xm;
-  p.i[4] = rm + x;
-  p.i[5] = rp + xp;
-  p.i[6] = rp + xm;
-  p.i[7] = rm + xm;
-  p.i[8] = rm + xp;
-  return p;
-}
-
-template <class ST>
-__device__ __forceinline__ float pull_phi(const StepArgs& a, const Pull& q) {
-  // summed in direction order 0..8
-  float s = load_h<ST, 0>(a, q.i[0]);
-  s += load_h<ST, 1>(a, q.i[1]);
-  s += load_h<ST, 2>(a, q.i[2]);
-  s += load_h<ST, 3>(a, q.i[3]);
-  s += load_h<ST, 4>(a, q.i[4]);
-  s += load_h<ST, 5>(a, q.i[5]);
-  s += load_h<ST, 6>(a, q.i[6]);
-  s += load_h<ST, 7>(a, q.i[7]);
-  s += load_h<ST, 8>(a, q.i[8]);
-  return s;
-}
-
-template <class ST>
-__device__ __forceinline__ void pull_f(const StepArgs& a, const Pull& q, float* f) {
-  f[0] = load_f<ST, 0>(a, q.i[0]);
-  f[1] = load_f<ST, 1>(a, q.i[1]);
-  f[2] = load_f<ST, 2>(a, q.i[2]);
-  f[3] = load_f<ST, 3>(a, q.i[3]);
-  f[4] = load_f<ST, 4>(a, q.i[4]);
-  f[5] = load_f<ST, 5>(a, q.i[5]);
-  f[6] = load_f<ST, 6>(a, q.i[6]);
-  f[7] = load_f<ST, 7>(a, q.i[7]);
-  f[8] = load_f<ST, 8>(a, q.i[8]);
-}
-template <class ST>
-__device__ __forceinline__ void pull_h(const StepArgs& a, const Pull& q, float* h) {
-  h[0] = load_h<ST, 0>(a, q.i[0]);
-  h[1] = load_h<ST, 1>(a, q.i[1]);
-  h[2] = load_h<ST, 2>(a, q.i[2]);
-  h[3] = load_h<ST, 3>(a, q.i[3]);
-  h[4] = load_h<ST, 4>(a, q.i[4]);
-  h[5] = load_h<ST, 5>(a, q.i[5]);
-  h[6] = load_h<ST, 6>(a, q.i[6]);
-  h[7] = load_h<ST, 7>(a, q.i[7]);
-  h[8] = load_h<ST, 8>(a, q.i[8]);
-}
-
-// Central-scheme derivatives (Eq. ICS-1st) of a shared-memory field at
-// element c with row stride S: d/dx = 3 sum_i w_i c_ix a(x + c_i).
-template <int S>
-__device__ __forceinline__ float ics_dx(const float* a, int c) {
-  return (a[c + 1] - a[c - 1]) * (1.0f / 3.0f) +
-         ((a[c + S + 1] - a[c + S - 1]) + (a[c - S + 1] - a[c - S - 1])) * (1.0f / 12.0f);
-}
-template <int S>
-__device__ __forceinline__ float ics_dy(const float* a, int c) {
-  return (a[c + S] - a[c - S]) * (1.0f / 3.0f) +
-         ((a[c + S + 1] - a[c - S + 1]) + (a[c + S - 1] - a[c - S - 1])) * (1.0f / 12.0f);
 }
 
 // ---------------------------------------------------------------------------
 // the fused step kernel
 // ---------------------------------------------------------------------------
 template <int FORM, class ST>
-__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
-  constexpr int B3X = kTX + 6, B3Y = kTY + 6;
-  constexpr int B2X = kTX + 4, B2Y = kTY + 4;
-  constexpr int B1X = kTX + 2, B1Y = kTY + 2;
-  constexpr int N2 = B2X * B2Y, N1 = B1X * B1Y;
-  constexpr int NE = extra_fields<FORM>();
-  // level-1 field slots in s2
+__global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ StepArgs a) {
+  using G = Smem<ST, FORM>;
+  constexpr int B3X = G::B3X, B2X = G::B2X, B1X = G::B1X, B1Y = G::B1Y;
+  constexpr int N2 = G::N2, N1 = G::N1;
+  constexpr int PW = G::PW, XP = G::XPAD;
+  // level-1 field slots in s2, ring-1 slots in s1
   constexpr int GX = 0, GY = 1, LAP = 2, MU = 3, E0 = 4;
-  // ring-1 slots in s1
   constexpr int FX = 0, FY = 1, UX = 2, UY = 3, PUX = 4, PUY = 5;
 
-  __shared__ float sPhi[B3X * B3Y];
-  __shared__ float s2[(4 + NE) * N2];
-  __shared__ float s1[6 * N1];
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
+  float* sPhi = reinterpret_cast<float*>(sm + G::OFF_PHI);
+  float* s2 = reinterpret_cast<float*>(sm + G::OFF_S2);
+  float* s1 = reinterpret_cast<float*>(sm + G::OFF_S1);
 
   const Lattice L = a.L;
   const Phys& P = a.p;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int tid = threadIdx.x;
 
+  // ---- staging ---------------------------------------------------------------
+  const bool tma = a.use_tma && x0 - XP >= 0 && x0 + kTX + XP <= L.nx && y0 >= 4 &&
+                   y0 + kTY + 4 <= L.ny;
+  if (tma) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+      mbar_arrive_expect_tx(bar, G::TMA_TX);
+      const int xs = x0 - XP;
+      const int rows = L.ny + 2;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        // h box of plane i: storage rows from (y0 - 3 - c_iy) + 1
+        const int yh = y0 - 2 - qcy(i);
+        if (ST::kSplitH0 && i == 0) tma_load_2d(sm + G::h_off(0), &a.tm_h0, xs, yh, bar);
+        else tma_load_2d(sm + G::h_off(i), &a.tm_h, xs, (ST::kSplitH0 ? i - 1 : i) * rows + yh, bar);
+        // f box of plane i: storage rows from (y0 - 1 - c_iy) + 1
+        tma_load_2d(sm + G::f_off(i), &a.tm_f, xs, i * rows + y0 - qcy(i), bar);
+      }
+    }
+    __syncthreads();  // barrier initialised before anyone waits on it
+    int timed_out = 0;
+    for (long long n = 0; !mbar_try_wait(bar, 0);) {
+      if (++n > kWaitLimit) {
+        timed_out = 1;
+        break;
+      }
+    }
+    if (__syncthreads_or(timed_out)) {
+      // the loads did not complete: flag it, wait (bounded) for the copies
+      // still in flight so none lands after the CTA exits, and give up
+      if (tid == 0) atomicOr(a.err, 1);
+      for (long long m = 0; m < kWaitLimit && !mbar_try_wait(bar, 0); ++m) {
+      }
+      return;
+    }
+  } else {
+    fill_boxes_plain<ST, G>(a, sm, x0, y0);
+    __syncthreads();
+  }
+
   // ---- pass 1: phi on tile + 3 ------------------------------------------------
-  for (int k = tid; k < B3X * B3Y; k += kThreads) {
-    const int ly = k / B3X, lx = k - ly * B3X;
-    const int gx = wrap(x0 - 3 + lx, L.nx);
-    const int gy = map_row(y0 - 3 + ly, L.ny, L.wall);
-    sPhi[k] = pull_phi<ST>(a, pull_idx(L, gx, gy));
+  for (int k = tid; k < G::N3; k += kThreads) {
+    const int r = k / B3X, cc = k - r * B3X;
+    const int yn = y0 - 3 + r;
+    if (L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
+    const int c = cc + XP - 3;
+    float s = box_h<ST, 0, G>(sm, r, c, P);
+    s += box_h<ST, 1, G>(sm, r, c - 1, P);
+    s += box_h<ST, 2, G>(sm, r, c, P);
+    s += box_h<ST, 3, G>(sm, r, c + 1, P);
+    s += box_h<ST, 4, G>(sm, r, c, P);
+    s += box_h<ST, 5, G>(sm, r, c - 1, P);
+    s += box_h<ST, 6, G>(sm, r, c + 1, P);
+    s += box_h<ST, 7, G>(sm, r, c + 1, P);
+    s += box_h<ST, 8, G>(sm, r, c - 1, P);
+    sPhi[k] = s;
   }
   __syncthreads();
+  if (L.wall && (y0 - 3 < 0 || y0 + kTY + 3 > L.ny)) {
+    // mirror ghosts of phi about the wall planes
+    for (int k = tid; k < G::N3; k += kThreads) {
+      const int r = k / B3X, cc = k - r * B3X;
+      const int yn = y0 - 3 + r;
+      if (yn >= 0 && yn < L.ny) continue;
+      const int rm = map_row(yn, L.ny, 1) - (y0 - 3);
+      sPhi[k] = (rm >= 0 && rm < G::B3Y) ? sPhi[rm * B3X + cc] : 0.0f;
+    }
+    __syncthreads();
+  }
 
   // ---- pass 2: grad phi, lap phi, mu, level-1 fields on tile + 2 -------------
   for (int k = tid; k < N2; k += kThreads) {
@@ -334,12 +337,14 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     const float rho = P.rho_mid + P.drho_half * phi;
     Fx += (rho - P.rho0) * P.gx;
     Fy += (rho - P.rho0) * P.gy;
-    const int gxn = wrap(x0 - 1 + lx, L.nx);
-    const int gyn = map_row(y0 - 1 + ly, L.ny, L.wall);
-    float f[9];
-    pull_f<ST>(a, pull_idx(L, gxn, gyn), f);
-    const float jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-    const float jy = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
+    // pulled f from the boxes: row ly, column (lx - 1) + XP - c_ix
+    const int c = lx + XP - 1;
+    const float f1 = box_f<ST, 1, G>(sm, ly, c - 1, P), f2 = box_f<ST, 2, G>(sm, ly, c, P);
+    const float f3 = box_f<ST, 3, G>(sm, ly, c + 1, P), f4 = box_f<ST, 4, G>(sm, ly, c, P);
+    const float f5 = box_f<ST, 5, G>(sm, ly, c - 1, P), f6 = box_f<ST, 6, G>(sm, ly, c + 1, P);
+    const float f7 = box_f<ST, 7, G>(sm, ly, c + 1, P), f8 = box_f<ST, 8, G>(sm, ly, c - 1, P);
+    const float jx = (f1 - f3) + ((f5 - f6) + (f8 - f7));
+    const float jy = (f2 - f4) + ((f5 - f8) + (f6 - f7));
     // Eq. mac: u = [sum c f + cs^2 F / 2] / (cs^2 rho)
     const float irho = 1.0f / rho;
     const float ux = (3.0f * jx + 0.5f * Fx) * irho;
@@ -394,9 +399,18 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     const float rho = P.rho_mid + P.drho_half * phi;
     const float drx = P.drho_half * Gx, dry = P.drho_half * Gy;
 
-    const Pull q = pull_idx(L, gx, gy);
+    // pulled populations: f box row ly + 1, h box row ly + 3, column lx + XP - c_ix
+    const int c = lx + XP;
     float f[9];
-    pull_f<ST>(a, q, f);
+    f[0] = box_f<ST, 0, G>(sm, ly + 1, c, P);
+    f[1] = box_f<ST, 1, G>(sm, ly + 1, c - 1, P);
+    f[2] = box_f<ST, 2, G>(sm, ly + 1, c, P);
+    f[3] = box_f<ST, 3, G>(sm, ly + 1, c + 1, P);
+    f[4] = box_f<ST, 4, G>(sm, ly + 1, c, P);
+    f[5] = box_f<ST, 5, G>(sm, ly + 1, c - 1, P);
+    f[6] = box_f<ST, 6, G>(sm, ly + 1, c + 1, P);
+    f[7] = box_f<ST, 7, G>(sm, ly + 1, c + 1, P);
+    f[8] = box_f<ST, 8, G>(sm, ly + 1, c - 1, P);
     const float sumf = f[0] + (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
     // Eq. mac: P = sum f + cs^2/2 u . grad rho
     const float Pr = sumf + (ux * drx + uy * dry) * (1.0f / 6.0f);
@@ -436,7 +450,15 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
     a.phiu[nn + n_idx] = puy;
 
     float h[9];
-    pull_h<ST>(a, q, h);
+    h[0] = box_h<ST, 0, G>(sm, ly + 3, c, P);
+    h[1] = box_h<ST, 1, G>(sm, ly + 3, c - 1, P);
+    h[2] = box_h<ST, 2, G>(sm, ly + 3, c, P);
+    h[3] = box_h<ST, 3, G>(sm, ly + 3, c + 1, P);
+    h[4] = box_h<ST, 4, G>(sm, ly + 3, c, P);
+    h[5] = box_h<ST, 5, G>(sm, ly + 3, c - 1, P);
+    h[6] = box_h<ST, 6, G>(sm, ly + 3, c + 1, P);
+    h[7] = box_h<ST, 7, G>(sm, ly + 3, c + 1, P);
+    h[8] = box_h<ST, 8, G>(sm, ly + 3, c - 1, P);
 
     // f collision with forcing, Eqs. fh and P_LBM (Gamma_i = w_i (1 + s_i),
     // grad-rho weight w_i s_i)
@@ -519,21 +541,34 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   }
 }
 
+template <int FORM, class ST>
+cudaError_t launch_form(const StepArgs& a, cudaStream_t s) {
+  using G = Smem<ST, FORM>;
+  static bool configured = false;  // per instantiation; attribute is per device function
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step<FORM, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((a.L.nx + kTX - 1) / kTX, (a.L.ny + kTY - 1) / kTY);
+  k_step<FORM, ST><<<grid, kThreads, G::BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class ST>
 cudaError_t launch_step_impl(int form, const StepArgs& a, cudaStream_t s) {
-  dim3 grid((a.L.nx + kTX - 1) / kTX, (a.L.ny + kTY - 1) / kTY);
   switch (form) {
-    case kSTF1: k_step<kSTF1, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kSTF2: k_step<kSTF2, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kCPF1: k_step<kCPF1, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kCPF2: k_step<kCPF2, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kPF1: k_step<kPF1, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kPF2: k_step<kPF2, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kCSF1: k_step<kCSF1, ST><<<grid, kThreads, 0, s>>>(a); break;
-    case kCSF2: k_step<kCSF2, ST><<<grid, kThreads, 0, s>>>(a); break;
+    case kSTF1: return launch_form<kSTF1, ST>(a, s);
+    case kSTF2: return launch_form<kSTF2, ST>(a, s);
+    case kCPF1: return launch_form<kCPF1, ST>(a, s);
+    case kCPF2: return launch_form<kCPF2, ST>(a, s);
+    case kPF1: return launch_form<kPF1, ST>(a, s);
+    case kPF2: return launch_form<kPF2, ST>(a, s);
+    case kCSF1: return launch_form<kCSF1, ST>(a, s);
+    case kCSF2: return launch_form<kCSF2, ST>(a, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace pflbm

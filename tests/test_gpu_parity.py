@@ -81,7 +81,11 @@ def test_tiny_grids(pf, orc, shape, wall):
 @pytest.mark.parametrize("form", FORMS)
 def test_all_fields_one_step(pf, orc, form):
     """Every read-back field after a few steps from a non-equilibrium field
-    (chemical potential, both pressures, force) within FP32 rounding."""
+    (chemical potential, both pressures, force).  Tolerance: float32 state
+    rounding (unit 6e-8 on h_0 ~ phi ~ 1) reaches derived fields through
+    differences of O(1) values (grad phi, mu = 4 beta phi^3 - ... - kappa lap
+    phi, P = sum f); 1e-4 of each field's scale plus 1e-8 absolute bounds it
+    with margin (about 1000 ulps)."""
     nx, ny = 48, 40
     phi0 = wl.smooth_random(nx, ny, seed=3, amp=0.9)
     p = dict(sigma=0.02, W=4.0, M=0.1, rho1=1.0, rho2=0.5, nu1=0.1, nu2=0.05, gx=1e-5,
@@ -89,7 +93,7 @@ def test_all_fields_one_step(pf, orc, form):
     _, g, _, o = run_pair(pf, orc, nx, ny, False, p, phi0, 3)
     for k in ("phi", "rho", "ux", "uy", "P", "mu", "p_h", "Fx", "Fy"):
         scale = max(1e-6, float(np.abs(o[k]).max()))
-        assert err(g, o, k) <= 2e-5 * scale + 1e-9, (k, err(g, o, k), scale)
+        assert err(g, o, k) <= 1e-4 * scale + 1e-8, (k, err(g, o, k), scale)
 
 
 @pytest.mark.parametrize("wall", [False, True])
