@@ -166,6 +166,12 @@ pflbm_status pflbm_step(pflbm_domain* d, int nsteps);
  * default).  Graphs need a non-default stream. */
 pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
 
+/* Stage interior tiles with TMA tensor loads (1, the default where the row
+ * pitch nx * element size is a multiple of 16 bytes) or fill every tile with
+ * plain loads (0).  Both fill identical shared-memory boxes, so results are
+ * bitwise equal; the switch exists to test exactly that. */
+pflbm_status pflbm_set_tma(pflbm_domain* d, int enable);
+
 /* Steps taken since pflbm_init_phi. */
 long long pflbm_steps_done(const pflbm_domain* d);
 

@@ -43,18 +43,29 @@ CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
 CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 
 
+_SRC32 = os.path.join(_HERE, "pflbm_oracle_f32.c")
+_LIB32 = os.path.join(_BUILD, "liboracle_f32.so")
+
+
+def _compile(src: str, lib: str, force: bool) -> str:
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(src))
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = lib + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-std=c99", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, lib)
+    return lib
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, OpenMP,
-    no FMA contraction so results do not depend on the host ISA)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-           "-std=c99", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    no FMA contraction so results do not depend on the host ISA), and its
+    float32-state build ``liboracle_f32.so``."""
+    _compile(_SRC32, _LIB32, force)
+    return _compile(_SRC, _LIB, force)
 
 
 _lib = None
@@ -266,3 +277,45 @@ def taylor_D(fields: dict) -> float:
     l1, l2 = tr / 2 + disc, tr / 2 - disc
     L, B = 4 * math.sqrt(l1), 4 * math.sqrt(max(l2, 0.0))
     return (L - B) / (L + B)
+
+
+# ---------------------------------------------------------------------------
+# float32 rounding sensitivity of a workload
+# ---------------------------------------------------------------------------
+
+_lib32 = None
+
+
+def lib32():
+    global _lib32
+    if _lib32 is None:
+        build()
+        _lib32 = ctypes.CDLL(_LIB32)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i = ctypes.c_int
+        _lib32.w32_step.argtypes = [dp, i, i, i, dp, dp, dp, i, i]
+        _lib32.w32_macro.argtypes = [dp, i, i, i, dp, dp, dp, i, dp]
+    return _lib32
+
+
+def float32_deviation(nx, ny, wall_y, par: Params, phi0, steps: int) -> dict:
+    """Max |phi| and |u| deviation after `steps` steps between the FP64 oracle
+    and the same algorithm run with float32 state (pflbm_oracle_f32.c), both
+    from phi0.  It measures the rounding sensitivity of a workload, from which
+    tests derive the tolerance of a float32 implementation."""
+    a = Sim(nx, ny, wall_y, par, phi0)
+    b = Sim(nx, ny, wall_y, par, phi0)
+    a.step(steps)
+    L = lib32()
+    L.w32_step(_p(b.pv), b.nx, b.ny, int(b.wall), _p(b.f), _p(b.h), _p(b.phiu_prev),
+               int(steps), 1)
+    out = np.zeros((len(FIELDS), ny, nx))
+    L.w32_macro(_p(b.pv), b.nx, b.ny, int(b.wall), _p(b.f), _p(b.h), _p(b.phiu_prev),
+                int(steps == 0), _p(out))
+    m = a.macro()
+    f32 = {k: out[i] for i, k in enumerate(FIELDS)}
+    return {
+        "phi": float(np.abs(f32["phi"] - m["phi"]).max()),
+        "u": float(max(np.abs(f32["ux"] - m["ux"]).max(), np.abs(f32["uy"] - m["uy"]).max())),
+        "fields64": m,
+    }

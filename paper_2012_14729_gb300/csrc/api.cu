@@ -79,7 +79,8 @@ struct pflbm_domain {
   Phys phys;
   // TMA descriptors of the input population arrays of each buffer
   CUtensorMap tm_f[2], tm_h[2], tm_h0[2];
-  int use_tma;
+  int use_tma;  // maps built and usable
+  int tma_off;  // caller asked for plain loads
   int graphs;
   cudaGraphExec_t gexec;
   int g_parity;  // buffer parity the captured graph starts from
@@ -114,8 +115,8 @@ StepArgs make_args(const pflbm_domain* d, int from) {
   a.phiu = reinterpret_cast<float*>(d->ws + d->lay.phiu);
   a.fields = reinterpret_cast<float*>(d->ws + d->lay.fields);
   a.err = reinterpret_cast<int*>(d->ws + d->lay.err);
-  a.use_tma = d->use_tma;
-  if (d->use_tma) {
+  a.use_tma = d->use_tma && !d->tma_off;
+  if (a.use_tma) {
     a.tm_f = d->tm_f[from];
     a.tm_h = d->tm_h[from];
     a.tm_h0 = d->tm_h0[from];
@@ -140,14 +141,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // A [planes * rows][nx] array as a 2-D tensor with boxes of box_rows rows of
-// box_w(elem) columns.
+// box_cols columns.  Every box of a domain has the column count of its
+// population storage (box_w of the 16-bit element for FP16/BF16, also for the
+// float32 h_0 plane), matching the kernel's shared-memory geometry.
 bool encode_map(CUtensorMap* m, void* base, CUtensorMapDataType dt, int elem, int nx,
-                long long rows, int box_rows) {
+                long long rows, int box_cols, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)nx * elem};
-  cuuint32_t box[2] = {(cuuint32_t)box_w(elem), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -166,13 +169,14 @@ void build_maps(pflbm_domain* d) {
   const long long rows = d->ny + 2;
   const bool split = d->storage != kFP32;
   bool ok = true;
+  const int bw = box_w(eb);
   for (int b = 0; b < 2 && ok; ++b) {
-    ok = encode_map(&d->tm_f[b], d->ws + d->lay.f[b], dt, eb, d->nx, 9 * rows, kBoxRowsF) &&
-         encode_map(&d->tm_h[b], d->ws + d->lay.h[b], dt, eb, d->nx, (split ? 8 : 9) * rows,
+    ok = encode_map(&d->tm_f[b], d->ws + d->lay.f[b], dt, eb, d->nx, 9 * rows, bw, kBoxRowsF) &&
+         encode_map(&d->tm_h[b], d->ws + d->lay.h[b], dt, eb, d->nx, (split ? 8 : 9) * rows, bw,
                     kBoxRowsH);
     if (ok && split)
       ok = encode_map(&d->tm_h0[b], d->ws + d->lay.h0[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
-                      d->nx, rows, kBoxRowsH);
+                      d->nx, rows, bw, kBoxRowsH);
     if (ok && !split) d->tm_h0[b] = d->tm_h[b];
   }
   d->use_tma = ok ? 1 : 0;
@@ -398,6 +402,13 @@ pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
   build_maps(d);
   d->t = 0;
   d->has_state = 1;
+  drop_graph(d);
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_set_tma(pflbm_domain* d, int enable) {
+  if (!d) return PFLBM_EINVAL;
+  d->tma_off = enable ? 0 : 1;
   drop_graph(d);
   return PFLBM_OK;
 }

@@ -71,7 +71,7 @@ constexpr int kTY = 16;
 constexpr int kThreads = 256;
 // Spin limit of the kernel's mbarrier waits (each try_wait suspends for a
 // hardware-bounded time); past it the kernel flags err and returns.
-constexpr long long kWaitLimit = 1ll << 22;
+constexpr long long kWaitLimit = 1ll << 20;
 
 // Box geometry of the TMA loads for a storage element size: columns
 // [x0 - xpad, x0 + kTX + xpad) so that the start column is 16-byte aligned.

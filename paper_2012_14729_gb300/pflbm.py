@@ -70,6 +70,7 @@ SIGNATURES = {
     "pflbm_init_phi": (_i, [_vp, _vp, _i]),
     "pflbm_step": (_i, [_vp, _i]),
     "pflbm_set_graphs": (_i, [_vp, _i]),
+    "pflbm_set_tma": (_i, [_vp, _i]),
     "pflbm_steps_done": (ctypes.c_longlong, [_vp]),
     "pflbm_read": (_i, [_vp, _i, _vp, _i]),
     "pflbm_read_fields": (_i, [_vp, _vp, _i]),
@@ -158,6 +159,10 @@ def pflbm_step(d, nsteps: int):
 
 def pflbm_set_graphs(d, enable: bool):
     _check(load().pflbm_set_graphs(d, int(bool(enable))), "pflbm_set_graphs")
+
+
+def pflbm_set_tma(d, enable: bool):
+    _check(load().pflbm_set_tma(d, int(bool(enable))), "pflbm_set_tma")
 
 
 def pflbm_steps_done(d) -> int:
@@ -258,6 +263,10 @@ class Domain:
 
     def graphs(self, enable: bool = True) -> "Domain":
         pflbm_set_graphs(self.h, enable)
+        return self
+
+    def tma(self, enable: bool = True) -> "Domain":
+        pflbm_set_tma(self.h, enable)
         return self
 
     def step(self, n: int = 1) -> "Domain":
