@@ -3,6 +3,20 @@
 
 namespace pflbm {
 
+// Streaming multiprocessors of the current device (persistent grid size).
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 1;
+  }
+  return n;
+}
+
 // ---------------------------------------------------------------------------
 // initial state (zero velocity, Sec. 5.1): f = f^eq(P = 0, u = 0) = 0 and
 // h = h^eq(phi0, mu0, 0) with mu0 = 4 beta phi0 (phi0^2 - 1) - kappa lap phi0.

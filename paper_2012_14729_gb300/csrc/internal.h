@@ -68,7 +68,7 @@ struct StepArgs {
 // Tile of the fused step kernel.
 constexpr int kTX = 32;
 constexpr int kTY = 16;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;  // one node per thread in the collision pass
 // Spin limit of the kernel's mbarrier waits (each try_wait suspends for a
 // hardware-bounded time); past it the kernel flags err and returns.
 constexpr long long kWaitLimit = 1ll << 20;

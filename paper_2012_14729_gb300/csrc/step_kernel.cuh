@@ -1,17 +1,19 @@
 // Fused coupled step of the phase-field lattice Boltzmann method (Sec. 3 of
 // Zhang, Liang & Guo, arXiv 2012.14729) for sm_103a.
 //
-// One CTA owns a kTX x kTY tile of nodes and runs the whole time step for it.
+// A persistent kernel: one 512-thread CTA per SM walks a list of kTX x kTY
+// tiles and runs the whole time step for each.
 //
 // Staging.  The post-collision populations of the previous step are brought
 // into shared memory as one 2-D box per population plane: h planes on the
 // tile + 3 ring (rows) and f planes on the tile + 1 ring, each box shifted by
 // -c_i in y so that its rows hold the pulled values; in x every box spans the
 // same 16-byte aligned column range and the -c_ix shift is applied when the
-// box is read.  Interior tiles issue the 18 boxes as TMA tensor loads
-// (cp.async.bulk.tensor) completing on one mbarrier; tiles whose boxes wrap
-// around the periodic seam or reach the wall ghost rows fill the same boxes
-// with plain loads.
+// box is read.  Interior tiles issue their 18 boxes as TMA tensor loads
+// (cp.async.bulk.tensor) completing on an mbarrier.  Two box buffers
+// alternate: while a CTA computes one tile, the TMA loads of its next tile
+// are in flight.  Tiles whose boxes wrap around the periodic seam or reach
+// the wall ghost rows fill the same boxes with plain loads.
 //
 // Passes over shared memory, recomputing the halo a tile's nodes need
 // instead of exchanging it through HBM:
@@ -50,6 +52,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (TMA) writes to it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
@@ -92,47 +99,73 @@ struct Smem {
   static constexpr int HB0 = pad128(RH * PW * (ST::kSplitH0 ? 4 : EB));
   static constexpr int HB = pad128(RH * PW * EB);
   static constexpr int FB = pad128(RF * PW * EB);
+  static constexpr int BUF = HB0 + 8 * HB + 9 * FB;  // one set of 18 boxes
   static constexpr int B3X = kTX + 6, B3Y = kTY + 6;
   static constexpr int B2X = kTX + 4, B2Y = kTY + 4;
   static constexpr int B1X = kTX + 2, B1Y = kTY + 2;
   static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
   static constexpr int NE = extra_fields<FORM>();
-  static constexpr int OFF_BAR = 0;
-  static constexpr int OFF_H = 128;
-  static constexpr int OFF_F = OFF_H + HB0 + 8 * HB;
-  static constexpr int OFF_PHI = OFF_F + 9 * FB;
+  static constexpr int OFF_BAR = 0;        // two mbarriers
+  static constexpr int OFF_BUF = 128;      // two box buffers
+  static constexpr int OFF_PHI = OFF_BUF + 2 * BUF;
   static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
   static constexpr int OFF_S1 = OFF_S2 + pad128((4 + NE) * N2 * 4);
   static constexpr int BYTES = OFF_S1 + pad128(6 * N1 * 4);
-  static constexpr int TMA_BYTES = HB0 + 8 * HB + 9 * FB;  // counted per box, padded
   static constexpr int TMA_TX = RH * PW * (ST::kSplitH0 ? 4 : EB) + 8 * RH * PW * EB +
                                 9 * RF * PW * EB;  // bytes the 18 loads deliver
 
-  __device__ static int h_off(int i) { return OFF_H + (i == 0 ? 0 : HB0 + (i - 1) * HB); }
-  __device__ static int f_off(int i) { return OFF_F + i * FB; }
+  __device__ static int h_off(int i) { return i == 0 ? 0 : HB0 + (i - 1) * HB; }
+  __device__ static int f_off(int i) { return HB0 + 8 * HB + i * FB; }
 };
 
-// population i of a box at (row, col), decoded to float
+// population i of a box set at (row, col), decoded to float
 template <class ST, int I, class G>
-__device__ __forceinline__ float box_h(const unsigned char* sm, int r, int c, const Phys& P) {
+__device__ __forceinline__ float box_h(const unsigned char* bx, int r, int c, const Phys& P) {
   if constexpr (ST::kSplitH0 && I == 0) {
-    return reinterpret_cast<const float*>(sm + G::h_off(0))[r * G::PW + c];
+    return reinterpret_cast<const float*>(bx + G::h_off(0))[r * G::PW + c];
   } else {
-    const typename ST::T v = reinterpret_cast<const typename ST::T*>(sm + G::h_off(I))[r * G::PW + c];
+    const typename ST::T v =
+        reinterpret_cast<const typename ST::T*>(bx + G::h_off(I))[r * G::PW + c];
     return ST::dec(v, qw(I) * P.inv_sh);
   }
 }
 template <class ST, int I, class G>
-__device__ __forceinline__ float box_f(const unsigned char* sm, int r, int c, const Phys& P) {
-  const typename ST::T v = reinterpret_cast<const typename ST::T*>(sm + G::f_off(I))[r * G::PW + c];
+__device__ __forceinline__ float box_f(const unsigned char* bx, int r, int c, const Phys& P) {
+  const typename ST::T v = reinterpret_cast<const typename ST::T*>(bx + G::f_off(I))[r * G::PW + c];
   return ST::dec(v, qw(I) * P.inv_sf);
+}
+
+// Tiles whose 18 boxes lie inside the stored planes without wrapping.
+template <class G>
+__device__ __forceinline__ bool tma_tile(const StepArgs& a, int x0, int y0) {
+  return a.use_tma && x0 - G::XPAD >= 0 && x0 + kTX + G::XPAD <= a.L.nx && y0 >= 4 &&
+         y0 + kTY + 4 <= a.L.ny;
+}
+
+// Issue the 18 box loads of the tile at (x0, y0) into box set bx (one thread).
+template <class ST, class G>
+__device__ __forceinline__ void issue_tma(const StepArgs& a, unsigned char* bx, uint64_t* bar,
+                                          int x0, int y0) {
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, G::TMA_TX);
+  const int xs = x0 - G::XPAD;
+  const int rows = a.L.ny + 2;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    // h box of plane i: storage rows from (y0 - 3 - c_iy) + 1
+    const int yh = y0 - 2 - qcy(i);
+    if (ST::kSplitH0 && i == 0) tma_load_2d(bx + G::h_off(0), &a.tm_h0, xs, yh, bar);
+    else tma_load_2d(bx + G::h_off(i), &a.tm_h, xs, (ST::kSplitH0 ? i - 1 : i) * rows + yh, bar);
+    // f box of plane i: storage rows from (y0 - 1 - c_iy) + 1
+    tma_load_2d(bx + G::f_off(i), &a.tm_f, xs, i * rows + y0 - qcy(i), bar);
+  }
 }
 
 // Fill the boxes with plain loads (tiles at the periodic seam or the walls).
 // Box row r of plane i holds storage row (node row - c_iy) + 1 of the rows
 // the tile needs; rows the tile never pulls (beyond a wall) are zero.
 template <class ST, class G>
-__device__ void fill_boxes_plain(const StepArgs& a, unsigned char* sm, int x0, int y0) {
+__device__ void fill_boxes_plain(const StepArgs& a, unsigned char* bx, int x0, int y0) {
   using T = typename ST::T;
   const Lattice& L = a.L;
   auto srow = [&](int yy) -> int {  // storage row of source domain row yy, or -1
@@ -147,11 +180,11 @@ __device__ void fill_boxes_plain(const StepArgs& a, unsigned char* sm, int x0, i
     for (int i = 0; i < 9; ++i) {
       const int sr = srow(yn - qcy(i));
       if (ST::kSplitH0 && i == 0) {
-        reinterpret_cast<float*>(sm + G::h_off(0))[e] = sr >= 0 ? a.h0_in[sr * L.nx + gx] : 0.0f;
+        reinterpret_cast<float*>(bx + G::h_off(0))[e] = sr >= 0 ? a.h0_in[sr * L.nx + gx] : 0.0f;
       } else {
         const int pl = ST::kSplitH0 ? i - 1 : i;
         const T* src = reinterpret_cast<const T*>(a.h_in) + (size_t)pl * L.plane;
-        reinterpret_cast<T*>(sm + G::h_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
+        reinterpret_cast<T*>(bx + G::h_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
       }
     }
   }
@@ -163,75 +196,82 @@ __device__ void fill_boxes_plain(const StepArgs& a, unsigned char* sm, int x0, i
     for (int i = 0; i < 9; ++i) {
       const int sr = srow(yn - qcy(i));
       const T* src = reinterpret_cast<const T*>(a.f_in) + (size_t)i * L.plane;
-      reinterpret_cast<T*>(sm + G::f_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
+      reinterpret_cast<T*>(bx + G::f_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
     }
   }
 }
 
+// Bounded wait for a box set; returns false (after flagging a.err and a
+// second bounded wait for copies still in flight) if it did not complete.
+__device__ __forceinline__ bool wait_boxes(const StepArgs& a, uint64_t* bar, uint32_t parity) {
+  int timed_out = 0;
+  for (long long n = 0; !mbar_try_wait(bar, parity);) {
+    if (++n > kWaitLimit) {
+      timed_out = 1;
+      break;
+    }
+  }
+  if (__syncthreads_or(timed_out)) {
+    if (threadIdx.x == 0) atomicOr(a.err, 1);
+    for (long long m = 0; m < kWaitLimit && !mbar_try_wait(bar, parity); ++m) {
+    }
+    return false;
+  }
+  return true;
+}
+
+// One collision of an opposite pair (i, j) with c_j = -c_i, w_j = w_i:
+// f_i^+ = f_i (1 - 1/tau_f) + f_i^eq / tau_f + (1 - 1/(2 tau_f)) F_i and the
+// same for h with tau_h and H_i (Eqs. fh, P_LBM, CH_LB_force, heq_CH).
+struct CollideConsts {
+  float ux, uy, Pr, rho3, uu15, Fx, Fy, uF, rx, ry, uR, omf, omf1, cff;
+  float phi3, emu, A, dtx, dty, omh, omh1, chh;
+};
+template <int I>
+__device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, float fj, float hi,
+                                             float hj, float& foi, float& foj, float& hoi,
+                                             float& hoj) {
+  constexpr float w = qw(I);
+  constexpr float cx = (float)qcx(I), cy = (float)qcy(I);
+  const float cu = cx * k.ux + cy * k.uy;
+  const float l = 3.0f * cu;
+  const float q = 4.5f * cu * cu - k.uu15;
+  const float si = q + l, sj = q - l;
+  const float cF = cx * k.Fx + cy * k.Fy;
+  const float cR = cx * k.rx + cy * k.ry;
+  const float feqi = w * (k.Pr + k.rho3 * si);
+  const float feqj = w * (k.Pr + k.rho3 * sj);
+  const float Fi = w * ((1.0f + si) * (cF - k.uF) + si * (cR - k.uR));
+  const float Fj = w * ((1.0f + sj) * (-cF - k.uF) + sj * (-cR - k.uR));
+  foi = fi * k.omf1 + feqi * k.omf + k.cff * Fi;
+  foj = fj * k.omf1 + feqj * k.omf + k.cff * Fj;
+  const float hc = k.phi3 * cu;
+  const float cdt = 3.0f * (cx * k.dtx + cy * k.dty);
+  const float heqi = w * (k.emu + hc), heqj = w * (k.emu - hc);
+  const float Hi = w * (k.A + cdt), Hj = w * (k.A - cdt);
+  hoi = hi * k.omh1 + heqi * k.omh + k.chh * Hi;
+  hoj = hj * k.omh1 + heqj * k.omh + k.chh * Hj;
+}
+
 // ---------------------------------------------------------------------------
-// the fused step kernel
+// one tile: passes 1-4 from the box set bx
 // ---------------------------------------------------------------------------
 template <int FORM, class ST>
-__global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ StepArgs a) {
+__device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char* bx,
+                                          unsigned char* sm, int x0, int y0) {
   using G = Smem<ST, FORM>;
   constexpr int B3X = G::B3X, B2X = G::B2X, B1X = G::B1X, B1Y = G::B1Y;
   constexpr int N2 = G::N2, N1 = G::N1;
-  constexpr int PW = G::PW, XP = G::XPAD;
+  constexpr int XP = G::XPAD;
   // level-1 field slots in s2, ring-1 slots in s1
   constexpr int GX = 0, GY = 1, LAP = 2, MU = 3, E0 = 4;
   constexpr int FX = 0, FY = 1, UX = 2, UY = 3, PUX = 4, PUY = 5;
-
-  extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
   float* sPhi = reinterpret_cast<float*>(sm + G::OFF_PHI);
   float* s2 = reinterpret_cast<float*>(sm + G::OFF_S2);
   float* s1 = reinterpret_cast<float*>(sm + G::OFF_S1);
-
-  const Lattice L = a.L;
+  const Lattice& L = a.L;
   const Phys& P = a.p;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int tid = threadIdx.x;
-
-  // ---- staging ---------------------------------------------------------------
-  const bool tma = a.use_tma && x0 - XP >= 0 && x0 + kTX + XP <= L.nx && y0 >= 4 &&
-                   y0 + kTY + 4 <= L.ny;
-  if (tma) {
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      fence_mbar_init();
-      mbar_arrive_expect_tx(bar, G::TMA_TX);
-      const int xs = x0 - XP;
-      const int rows = L.ny + 2;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        // h box of plane i: storage rows from (y0 - 3 - c_iy) + 1
-        const int yh = y0 - 2 - qcy(i);
-        if (ST::kSplitH0 && i == 0) tma_load_2d(sm + G::h_off(0), &a.tm_h0, xs, yh, bar);
-        else tma_load_2d(sm + G::h_off(i), &a.tm_h, xs, (ST::kSplitH0 ? i - 1 : i) * rows + yh, bar);
-        // f box of plane i: storage rows from (y0 - 1 - c_iy) + 1
-        tma_load_2d(sm + G::f_off(i), &a.tm_f, xs, i * rows + y0 - qcy(i), bar);
-      }
-    }
-    __syncthreads();  // barrier initialised before anyone waits on it
-    int timed_out = 0;
-    for (long long n = 0; !mbar_try_wait(bar, 0);) {
-      if (++n > kWaitLimit) {
-        timed_out = 1;
-        break;
-      }
-    }
-    if (__syncthreads_or(timed_out)) {
-      // the loads did not complete: flag it, wait (bounded) for the copies
-      // still in flight so none lands after the CTA exits, and give up
-      if (tid == 0) atomicOr(a.err, 1);
-      for (long long m = 0; m < kWaitLimit && !mbar_try_wait(bar, 0); ++m) {
-      }
-      return;
-    }
-  } else {
-    fill_boxes_plain<ST, G>(a, sm, x0, y0);
-    __syncthreads();
-  }
 
   // ---- pass 1: phi on tile + 3 ------------------------------------------------
   for (int k = tid; k < G::N3; k += kThreads) {
@@ -239,15 +279,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ St
     const int yn = y0 - 3 + r;
     if (L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
     const int c = cc + XP - 3;
-    float s = box_h<ST, 0, G>(sm, r, c, P);
-    s += box_h<ST, 1, G>(sm, r, c - 1, P);
-    s += box_h<ST, 2, G>(sm, r, c, P);
-    s += box_h<ST, 3, G>(sm, r, c + 1, P);
-    s += box_h<ST, 4, G>(sm, r, c, P);
-    s += box_h<ST, 5, G>(sm, r, c - 1, P);
-    s += box_h<ST, 6, G>(sm, r, c + 1, P);
-    s += box_h<ST, 7, G>(sm, r, c + 1, P);
-    s += box_h<ST, 8, G>(sm, r, c - 1, P);
+    float s = box_h<ST, 0, G>(bx, r, c, P);
+    s += box_h<ST, 1, G>(bx, r, c - 1, P);
+    s += box_h<ST, 2, G>(bx, r, c, P);
+    s += box_h<ST, 3, G>(bx, r, c + 1, P);
+    s += box_h<ST, 4, G>(bx, r, c, P);
+    s += box_h<ST, 5, G>(bx, r, c - 1, P);
+    s += box_h<ST, 6, G>(bx, r, c + 1, P);
+    s += box_h<ST, 7, G>(bx, r, c + 1, P);
+    s += box_h<ST, 8, G>(bx, r, c - 1, P);
     sPhi[k] = s;
   }
   __syncthreads();
@@ -339,14 +379,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ St
     Fy += (rho - P.rho0) * P.gy;
     // pulled f from the boxes: row ly, column (lx - 1) + XP - c_ix
     const int c = lx + XP - 1;
-    const float f1 = box_f<ST, 1, G>(sm, ly, c - 1, P), f2 = box_f<ST, 2, G>(sm, ly, c, P);
-    const float f3 = box_f<ST, 3, G>(sm, ly, c + 1, P), f4 = box_f<ST, 4, G>(sm, ly, c, P);
-    const float f5 = box_f<ST, 5, G>(sm, ly, c - 1, P), f6 = box_f<ST, 6, G>(sm, ly, c + 1, P);
-    const float f7 = box_f<ST, 7, G>(sm, ly, c + 1, P), f8 = box_f<ST, 8, G>(sm, ly, c - 1, P);
+    const float f1 = box_f<ST, 1, G>(bx, ly, c - 1, P), f2 = box_f<ST, 2, G>(bx, ly, c, P);
+    const float f3 = box_f<ST, 3, G>(bx, ly, c + 1, P), f4 = box_f<ST, 4, G>(bx, ly, c, P);
+    const float f5 = box_f<ST, 5, G>(bx, ly, c - 1, P), f6 = box_f<ST, 6, G>(bx, ly, c + 1, P);
+    const float f7 = box_f<ST, 7, G>(bx, ly, c + 1, P), f8 = box_f<ST, 8, G>(bx, ly, c - 1, P);
     const float jx = (f1 - f3) + ((f5 - f6) + (f8 - f7));
     const float jy = (f2 - f4) + ((f5 - f8) + (f6 - f7));
     // Eq. mac: u = [sum c f + cs^2 F / 2] / (cs^2 rho)
-    const float irho = 1.0f / rho;
+    const float irho = __fdividef(1.0f, rho);
     const float ux = (3.0f * jx + 0.5f * Fx) * irho;
     const float uy = (3.0f * jy + 0.5f * Fy) * irho;
     s1[FX * N1 + k] = Fx;
@@ -401,17 +441,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ St
 
     // pulled populations: f box row ly + 1, h box row ly + 3, column lx + XP - c_ix
     const int c = lx + XP;
-    float f[9];
-    f[0] = box_f<ST, 0, G>(sm, ly + 1, c, P);
-    f[1] = box_f<ST, 1, G>(sm, ly + 1, c - 1, P);
-    f[2] = box_f<ST, 2, G>(sm, ly + 1, c, P);
-    f[3] = box_f<ST, 3, G>(sm, ly + 1, c + 1, P);
-    f[4] = box_f<ST, 4, G>(sm, ly + 1, c, P);
-    f[5] = box_f<ST, 5, G>(sm, ly + 1, c - 1, P);
-    f[6] = box_f<ST, 6, G>(sm, ly + 1, c + 1, P);
-    f[7] = box_f<ST, 7, G>(sm, ly + 1, c + 1, P);
-    f[8] = box_f<ST, 8, G>(sm, ly + 1, c - 1, P);
-    const float sumf = f[0] + (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+    const float f0 = box_f<ST, 0, G>(bx, ly + 1, c, P);
+    const float f1 = box_f<ST, 1, G>(bx, ly + 1, c - 1, P);
+    const float f2 = box_f<ST, 2, G>(bx, ly + 1, c, P);
+    const float f3 = box_f<ST, 3, G>(bx, ly + 1, c + 1, P);
+    const float f4 = box_f<ST, 4, G>(bx, ly + 1, c, P);
+    const float f5 = box_f<ST, 5, G>(bx, ly + 1, c - 1, P);
+    const float f6 = box_f<ST, 6, G>(bx, ly + 1, c + 1, P);
+    const float f7 = box_f<ST, 7, G>(bx, ly + 1, c + 1, P);
+    const float f8 = box_f<ST, 8, G>(bx, ly + 1, c - 1, P);
+    const float sumf = f0 + (f1 + f2 + f3 + f4) + (f5 + f6 + f7 + f8);
     // Eq. mac: P = sum f + cs^2/2 u . grad rho
     const float Pr = sumf + (ux * drx + uy * dry) * (1.0f / 6.0f);
     // div(phi u) by Eq. ICS-1st on the ring-1 values
@@ -427,11 +466,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ St
     if (a.macro) {
       const float g2 = Gx * Gx + Gy * Gy;
       const float om = (1.0f - phi) * (1.0f + phi);
-      const float f0 = 0.25f * P.beta4 * om * om;
+      const float f0e = 0.25f * P.beta4 * om * om;
       float ph = Pr;
       if constexpr (FORM == kSTF1) ph = Pr - P.kappa * g2;
-      if constexpr (FORM == kCPF1) ph = Pr - f0 + phi * mu + 0.5f * P.kappa * g2;
-      if constexpr (FORM == kCPF2) ph = Pr - f0 + 0.5f * P.kappa * g2;
+      if constexpr (FORM == kCPF1) ph = Pr - f0e + phi * mu + 0.5f * P.kappa * g2;
+      if constexpr (FORM == kCPF2) ph = Pr - f0e + 0.5f * P.kappa * g2;
       if constexpr (FORM == kPF1) ph = Pr + 0.5f * P.kappa * g2;
       if constexpr (FORM == kPF2) ph = Pr - P.kappa * phi * s2[LAP * N2 + c2] + 0.5f * P.kappa * g2;
       float* o = a.fields + n_idx;
@@ -449,52 +488,58 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ St
     a.phiu[n_idx] = pux;
     a.phiu[nn + n_idx] = puy;
 
-    float h[9];
-    h[0] = box_h<ST, 0, G>(sm, ly + 3, c, P);
-    h[1] = box_h<ST, 1, G>(sm, ly + 3, c - 1, P);
-    h[2] = box_h<ST, 2, G>(sm, ly + 3, c, P);
-    h[3] = box_h<ST, 3, G>(sm, ly + 3, c + 1, P);
-    h[4] = box_h<ST, 4, G>(sm, ly + 3, c, P);
-    h[5] = box_h<ST, 5, G>(sm, ly + 3, c - 1, P);
-    h[6] = box_h<ST, 6, G>(sm, ly + 3, c + 1, P);
-    h[7] = box_h<ST, 7, G>(sm, ly + 3, c + 1, P);
-    h[8] = box_h<ST, 8, G>(sm, ly + 3, c - 1, P);
+    const float h0 = box_h<ST, 0, G>(bx, ly + 3, c, P);
+    const float h1 = box_h<ST, 1, G>(bx, ly + 3, c - 1, P);
+    const float h2 = box_h<ST, 2, G>(bx, ly + 3, c, P);
+    const float h3 = box_h<ST, 3, G>(bx, ly + 3, c + 1, P);
+    const float h4 = box_h<ST, 4, G>(bx, ly + 3, c, P);
+    const float h5 = box_h<ST, 5, G>(bx, ly + 3, c - 1, P);
+    const float h6 = box_h<ST, 6, G>(bx, ly + 3, c + 1, P);
+    const float h7 = box_h<ST, 7, G>(bx, ly + 3, c + 1, P);
+    const float h8 = box_h<ST, 8, G>(bx, ly + 3, c - 1, P);
 
-    // f collision with forcing, Eqs. fh and P_LBM (Gamma_i = w_i (1 + s_i),
-    // grad-rho weight w_i s_i)
+    // relaxation constants: tau_f = 1/2 + mu(phi) / (cs^2 rho) (Sec. 3)
     const float mv = P.mu_mid + P.mu_dhalf * phi;
-    const float tauf = 0.5f + 3.0f * mv * (1.0f / rho);
-    const float omf = 1.0f / tauf;
-    const float cff = 1.0f - 0.5f * omf;
-    const float uu15 = 1.5f * (ux * ux + uy * uy);
-    const float uF = ux * Fx + uy * Fy;
-    const float rx = drx * (1.0f / 3.0f), ry = dry * (1.0f / 3.0f);
-    const float uR = ux * rx + uy * ry;
-    const float rho3 = rho * (1.0f / 3.0f);
-    // h collision with the CH source, Eqs. fh, heq_CH and CH_LB_force
-    const float emu = P.eta * mu;
-    const float A = P.acoef * div;
-    const float omh = P.inv_tau_h, chh = P.hforce;
+    const float omf = __fdividef(1.0f, 0.5f + 3.0f * mv * __fdividef(1.0f, rho));
+    CollideConsts K;
+    K.ux = ux;
+    K.uy = uy;
+    K.Pr = Pr;
+    K.rho3 = rho * (1.0f / 3.0f);
+    K.uu15 = 1.5f * (ux * ux + uy * uy);
+    K.Fx = Fx;
+    K.Fy = Fy;
+    K.uF = ux * Fx + uy * Fy;
+    K.rx = drx * (1.0f / 3.0f);
+    K.ry = dry * (1.0f / 3.0f);
+    K.uR = ux * K.rx + uy * K.ry;
+    K.omf = omf;
+    K.omf1 = 1.0f - omf;
+    K.cff = 1.0f - 0.5f * omf;
+    K.phi3 = 3.0f * phi;
+    K.emu = P.eta * mu;
+    K.A = P.acoef * div;
+    K.dtx = dtx;
+    K.dty = dty;
+    K.omh = P.inv_tau_h;
+    K.omh1 = 1.0f - P.inv_tau_h;
+    K.chh = P.hforce;
 
     float fo[9], ho[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const float cxi = (float)qcx(i), cyi = (float)qcy(i), wi = qw(i);
-      const float cu = cxi * ux + cyi * uy;
-      const float s = cu * (3.0f + 4.5f * cu) - uu15;
-      const float feq = wi * (Pr + rho3 * s);
-      const float Fi = wi * ((1.0f + s) * (cxi * Fx + cyi * Fy - uF) + s * (cxi * rx + cyi * ry - uR));
-      fo[i] = f[i] - (f[i] - feq) * omf + cff * Fi;
-      float heq, Hi;
-      if (i == 0) {
-        heq = phi + (wi - 1.0f) * emu;
-        Hi = (wi - 1.0f) * A;
-      } else {
-        heq = wi * (emu + 3.0f * phi * cu);
-        Hi = wi * (A + 3.0f * (cxi * dtx + cyi * dty));
-      }
-      ho[i] = h[i] - (h[i] - heq) * omh + chh * Hi;
+    {
+      // rest population: s_0 = -1.5 |u|^2, c_0 = 0, wbar_0 = w_0 - 1
+      constexpr float w0 = qw(0);
+      const float s0 = -K.uu15;
+      const float feq0 = w0 * (Pr + K.rho3 * s0);
+      const float F0 = w0 * ((1.0f + s0) * (-K.uF) + s0 * (-K.uR));
+      fo[0] = f0 * K.omf1 + feq0 * omf + K.cff * F0;
+      const float heq0 = phi + (w0 - 1.0f) * K.emu;
+      ho[0] = h0 * K.omh1 + heq0 * K.omh + K.chh * ((w0 - 1.0f) * K.A);
     }
+    collide_pair<1>(K, f1, f3, h1, h3, fo[1], fo[3], ho[1], ho[3]);
+    collide_pair<2>(K, f2, f4, h2, h4, fo[2], fo[4], ho[2], ho[4]);
+    collide_pair<5>(K, f5, f7, h5, h7, fo[5], fo[7], ho[5], ho[7]);
+    collide_pair<6>(K, f6, f8, h6, h8, fo[6], fo[8], ho[6], ho[8]);
 
     const int o = (gy + 1) * L.nx + gx;
     store_f<ST, 0>(a, o, fo[0]); store_h<ST, 0>(a, o, ho[0]);
@@ -541,6 +586,71 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const __grid_constant__ St
   }
 }
 
+// ---------------------------------------------------------------------------
+// the persistent step kernel
+// ---------------------------------------------------------------------------
+template <int FORM, class ST>
+__global__ void __launch_bounds__(kThreads, 1) k_step(const __grid_constant__ StepArgs a) {
+  using G = Smem<ST, FORM>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
+  unsigned char* bufs = sm + G::OFF_BUF;
+
+  const int ntx = (a.L.nx + kTX - 1) / kTX;
+  const int ntiles = ntx * ((a.L.ny + kTY - 1) / kTY);
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t parity = 0u;
+  int buf = 0;
+  int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
+  bool tma_cur = tma_tile<G>(a, x0, y0);
+  if (tma_cur) {
+    if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs, &bars[0], x0, y0);
+  } else {
+    fill_boxes_plain<ST, G>(a, bufs, x0, y0);
+    __syncthreads();
+  }
+
+  for (;;) {
+    unsigned char* bx = bufs + buf * G::BUF;
+    if (tma_cur) {
+      // phase parity of each buffer's barrier, kept in two bits of `parity`
+      if (!wait_boxes(a, &bars[buf], (parity >> buf) & 1u)) return;
+      parity ^= 1u << buf;
+    }
+    // prefetch the next tile into the other buffer (its last reader, the
+    // tile before this one, finished at the barrier closing that tile)
+    const int tn = t + gridDim.x;
+    const int xn = (tn % ntx) * kTX, yn = (tn / ntx) * kTY;
+    const bool tma_next = tn < ntiles && tma_tile<G>(a, xn, yn);
+    if (tma_next && threadIdx.x == 0)
+      issue_tma<ST, G>(a, bufs + (buf ^ 1) * G::BUF, &bars[buf ^ 1], xn, yn);
+
+    step_tile<FORM, ST>(a, bx, sm, x0, y0);
+    __syncthreads();
+
+    if (tn >= ntiles) break;
+    if (!tma_next) {
+      fill_boxes_plain<ST, G>(a, bufs + (buf ^ 1) * G::BUF, xn, yn);
+      __syncthreads();
+    }
+    t = tn;
+    x0 = xn;
+    y0 = yn;
+    tma_cur = tma_next;
+    buf ^= 1;
+  }
+}
+
+int num_sms();
+
 template <int FORM, class ST>
 cudaError_t launch_form(const StepArgs& a, cudaStream_t s) {
   using G = Smem<ST, FORM>;
@@ -551,7 +661,8 @@ cudaError_t launch_form(const StepArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((a.L.nx + kTX - 1) / kTX, (a.L.ny + kTY - 1) / kTY);
+  const int ntiles = ((a.L.nx + kTX - 1) / kTX) * ((a.L.ny + kTY - 1) / kTY);
+  const int grid = ntiles < num_sms() ? ntiles : num_sms();
   k_step<FORM, ST><<<grid, kThreads, G::BYTES, s>>>(a);
   return cudaGetLastError();
 }
