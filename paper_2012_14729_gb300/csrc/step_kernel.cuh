@@ -201,6 +201,52 @@ __device__ void fill_boxes_plain(const StepArgs& a, unsigned char* bx, int x0, i
   }
 }
 
+// Asynchronous version of fill_boxes_plain for 4-byte storage: each element
+// is one cp.async (zero-filled when the source row is beyond a wall), so
+// seam and wall tiles are prefetched like TMA tiles.  Completion: each
+// thread's cp.async.wait_all, then a CTA barrier.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+template <class ST, class G>
+__device__ void fill_boxes_async(const StepArgs& a, unsigned char* bx, int x0, int y0) {
+  static_assert(sizeof(typename ST::T) == 4, "cp.async path is for 4-byte storage");
+  const Lattice& L = a.L;
+  auto srow = [&](int yy) -> int {
+    if (L.wall) return (yy >= -1 && yy <= L.ny) ? yy + 1 : -1;
+    return wrap(yy, L.ny) + 1;
+  };
+  const float* hin = reinterpret_cast<const float*>(a.h_in);
+  const float* fin = reinterpret_cast<const float*>(a.f_in);
+  for (int e = threadIdx.x; e < G::RH * G::PW; e += kThreads) {
+    const int r = e / G::PW, c = e - r * G::PW;
+    const int gx = wrap(x0 - G::XPAD + c, L.nx);
+    const int yn = y0 - 3 + r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int sr = srow(yn - qcy(i));
+      const float* src = hin + (size_t)i * L.plane + (sr >= 0 ? sr * L.nx + gx : 0);
+      cp_async4(reinterpret_cast<float*>(bx + G::h_off(i)) + e, src, sr >= 0);
+    }
+  }
+  for (int e = threadIdx.x; e < G::RF * G::PW; e += kThreads) {
+    const int r = e / G::PW, c = e - r * G::PW;
+    const int gx = wrap(x0 - G::XPAD + c, L.nx);
+    const int yn = y0 - 1 + r;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int sr = srow(yn - qcy(i));
+      const float* src = fin + (size_t)i * L.plane + (sr >= 0 ? sr * L.nx + gx : 0);
+      cp_async4(reinterpret_cast<float*>(bx + G::f_off(i)) + e, src, sr >= 0);
+    }
+  }
+}
+
 // Bounded wait for a box set; returns false (after flagging a.err and a
 // second bounded wait for copies still in flight) if it did not complete.
 __device__ __forceinline__ bool wait_boxes(const StepArgs& a, uint64_t* bar, uint32_t parity) {
@@ -272,6 +318,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
   const Lattice& L = a.L;
   const Phys& P = a.p;
   const int tid = threadIdx.x;
+  static_assert(kTX * kTY == kThreads, "one collision node per thread");
+
+  // (phi u)^{t-1} of this thread's collision node, loaded first so that the
+  // load latency overlaps passes 1-3
+  const int nn = L.nx * L.ny;
+  float pu_prev_x = 0.0f, pu_prev_y = 0.0f;
+  {
+    const int gx = x0 + tid % kTX, gy = y0 + tid / kTX;
+    if (!a.first && !a.macro && gx < L.nx && gy < L.ny) {
+      pu_prev_x = a.phiu[gy * L.nx + gx];
+      pu_prev_y = a.phiu[nn + gy * L.nx + gx];
+    }
+  }
 
   // ---- pass 1: phi on tile + 3 ------------------------------------------------
   for (int k = tid; k < G::N3; k += kThreads) {
@@ -424,7 +483,6 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
   }
 
   // ---- pass 4: collide and store on the tile --------------------------------
-  const int nn = L.nx * L.ny;
   for (int k = tid; k < kTX * kTY; k += kThreads) {
     const int ly = k / kTX, lx = k - ly * kTX;
     const int gx = x0 + lx, gy = y0 + ly;
@@ -459,8 +517,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
     const float pux = phi * ux, puy = phi * uy;
     float dtx = 0.0f, dty = 0.0f;
     if (!a.first) {
-      dtx = pux - a.phiu[n_idx];
-      dty = puy - a.phiu[nn + n_idx];
+      dtx = pux - pu_prev_x;
+      dty = puy - pu_prev_y;
     }
 
     if (a.macro) {
@@ -607,12 +665,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_step(const __grid_constant__ St
   }
   __syncthreads();
 
+  // seam and wall tiles of 4-byte storage are prefetched with cp.async;
+  // for 16-bit storage they are filled synchronously before use
+  constexpr bool kAsyncFill = sizeof(typename ST::T) == 4;
   uint32_t parity = 0u;
   int buf = 0;
   int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
   bool tma_cur = tma_tile<G>(a, x0, y0);
   if (tma_cur) {
     if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs, &bars[0], x0, y0);
+  } else if constexpr (kAsyncFill) {
+    fill_boxes_async<ST, G>(a, bufs, x0, y0);
   } else {
     fill_boxes_plain<ST, G>(a, bufs, x0, y0);
     __syncthreads();
@@ -624,22 +687,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_step(const __grid_constant__ St
       // phase parity of each buffer's barrier, kept in two bits of `parity`
       if (!wait_boxes(a, &bars[buf], (parity >> buf) & 1u)) return;
       parity ^= 1u << buf;
+    } else if constexpr (kAsyncFill) {
+      cp_async_wait_all();
+      __syncthreads();
     }
     // prefetch the next tile into the other buffer (its last reader, the
     // tile before this one, finished at the barrier closing that tile)
     const int tn = t + gridDim.x;
     const int xn = (tn % ntx) * kTX, yn = (tn / ntx) * kTY;
     const bool tma_next = tn < ntiles && tma_tile<G>(a, xn, yn);
-    if (tma_next && threadIdx.x == 0)
-      issue_tma<ST, G>(a, bufs + (buf ^ 1) * G::BUF, &bars[buf ^ 1], xn, yn);
+    if (tma_next) {
+      if (threadIdx.x == 0)
+        issue_tma<ST, G>(a, bufs + (buf ^ 1) * G::BUF, &bars[buf ^ 1], xn, yn);
+    } else if constexpr (kAsyncFill) {
+      if (tn < ntiles) fill_boxes_async<ST, G>(a, bufs + (buf ^ 1) * G::BUF, xn, yn);
+    }
 
     step_tile<FORM, ST>(a, bx, sm, x0, y0);
     __syncthreads();
 
     if (tn >= ntiles) break;
-    if (!tma_next) {
-      fill_boxes_plain<ST, G>(a, bufs + (buf ^ 1) * G::BUF, xn, yn);
-      __syncthreads();
+    if constexpr (!kAsyncFill) {
+      if (!tma_next) {
+        fill_boxes_plain<ST, G>(a, bufs + (buf ^ 1) * G::BUF, xn, yn);
+        __syncthreads();
+      }
     }
     t = tn;
     x0 = xn;
