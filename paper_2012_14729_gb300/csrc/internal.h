@@ -69,6 +69,11 @@ struct StepArgs {
 constexpr int kTX = 32;
 constexpr int kTY = 16;
 constexpr int kThreads = 512;  // one node per thread in the collision pass
+// Box buffers per CTA: 2 = the next tile's loads fly during this tile's
+// compute (one CTA per SM); 1 = two CTAs per SM overlap each other's loads
+// and compute.
+constexpr int kBoxBuffers = 1;
+constexpr int kMinBlocks = kBoxBuffers == 1 ? 2 : 1;
 // Spin limit of the kernel's mbarrier waits (each try_wait suspends for a
 // hardware-bounded time); past it the kernel flags err and returns.
 constexpr long long kWaitLimit = 1ll << 20;

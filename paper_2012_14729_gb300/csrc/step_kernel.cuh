@@ -107,7 +107,7 @@ struct Smem {
   static constexpr int NE = extra_fields<FORM>();
   static constexpr int OFF_BAR = 0;        // two mbarriers
   static constexpr int OFF_BUF = 128;      // two box buffers
-  static constexpr int OFF_PHI = OFF_BUF + 2 * BUF;
+  static constexpr int OFF_PHI = OFF_BUF + kBoxBuffers * BUF;
   static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
   static constexpr int OFF_S1 = OFF_S2 + pad128((4 + NE) * N2 * 4);
   static constexpr int BYTES = OFF_S1 + pad128(6 * N1 * 4);
@@ -648,7 +648,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
 // the persistent step kernel
 // ---------------------------------------------------------------------------
 template <int FORM, class ST>
-__global__ void __launch_bounds__(kThreads, 1) k_step(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_step(const __grid_constant__ StepArgs a) {
   using G = Smem<ST, FORM>;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
@@ -691,25 +691,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_step(const __grid_constant__ St
       cp_async_wait_all();
       __syncthreads();
     }
-    // prefetch the next tile into the other buffer (its last reader, the
-    // tile before this one, finished at the barrier closing that tile)
     const int tn = t + gridDim.x;
     const int xn = (tn % ntx) * kTX, yn = (tn / ntx) * kTY;
     const bool tma_next = tn < ntiles && tma_tile<G>(a, xn, yn);
-    if (tma_next) {
-      if (threadIdx.x == 0)
-        issue_tma<ST, G>(a, bufs + (buf ^ 1) * G::BUF, &bars[buf ^ 1], xn, yn);
-    } else if constexpr (kAsyncFill) {
-      if (tn < ntiles) fill_boxes_async<ST, G>(a, bufs + (buf ^ 1) * G::BUF, xn, yn);
+    const int nb = kBoxBuffers == 2 ? buf ^ 1 : 0;  // buffer of the next tile
+    if constexpr (kBoxBuffers == 2) {
+      // prefetch the next tile into the other buffer (its last reader, the
+      // tile before this one, finished at the barrier closing that tile)
+      if (tma_next) {
+        if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs + nb * G::BUF, &bars[nb], xn, yn);
+      } else if constexpr (kAsyncFill) {
+        if (tn < ntiles) fill_boxes_async<ST, G>(a, bufs + nb * G::BUF, xn, yn);
+      }
     }
 
     step_tile<FORM, ST>(a, bx, sm, x0, y0);
     __syncthreads();
 
     if (tn >= ntiles) break;
-    if constexpr (!kAsyncFill) {
+    if constexpr (kBoxBuffers == 1) {
+      // single buffer: stage the next tile now that this one is done
+      if (tma_next) {
+        if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs, &bars[0], xn, yn);
+      } else if constexpr (kAsyncFill) {
+        fill_boxes_async<ST, G>(a, bufs, xn, yn);
+      } else {
+        fill_boxes_plain<ST, G>(a, bufs, xn, yn);
+        __syncthreads();
+      }
+    } else if constexpr (!kAsyncFill) {
       if (!tma_next) {
-        fill_boxes_plain<ST, G>(a, bufs + (buf ^ 1) * G::BUF, xn, yn);
+        fill_boxes_plain<ST, G>(a, bufs + nb * G::BUF, xn, yn);
         __syncthreads();
       }
     }
@@ -717,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_step(const __grid_constant__ St
     x0 = xn;
     y0 = yn;
     tma_cur = tma_next;
-    buf ^= 1;
+    buf = nb;
   }
 }
 
@@ -734,7 +746,8 @@ cudaError_t launch_form(const StepArgs& a, cudaStream_t s) {
     configured = true;
   }
   const int ntiles = ((a.L.nx + kTX - 1) / kTX) * ((a.L.ny + kTY - 1) / kTY);
-  const int grid = ntiles < num_sms() ? ntiles : num_sms();
+  const int slots = num_sms() * kMinBlocks;
+  const int grid = ntiles < slots ? ntiles : slots;
   k_step<FORM, ST><<<grid, kThreads, G::BYTES, s>>>(a);
   return cudaGetLastError();
 }
