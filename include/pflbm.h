@@ -166,10 +166,27 @@ pflbm_status pflbm_step(pflbm_domain* d, int nsteps);
  * default).  Graphs need a non-default stream. */
 pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
 
-/* Stage interior tiles with TMA tensor loads (1, the default where the row
- * pitch nx * element size is a multiple of 16 bytes) or fill every tile with
- * plain loads (0).  Both fill identical shared-memory boxes, so results are
- * bitwise equal; the switch exists to test exactly that. */
+/* How the fused step kernel obtains the populations it pulls:
+ *   PFLBM_STAGE_BOXES   TMA box loads of each tile's population planes into
+ *                       shared memory, persistent CTAs (2 per SM)
+ *   PFLBM_STAGE_GATHER  L1-cached gathers straight from the planes, one CTA
+ *                       per tile (the default)
+ * Both compute the same step; results agree to float32 rounding order. */
+enum { PFLBM_STAGE_BOXES = 0, PFLBM_STAGE_GATHER = 1 };
+pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode);
+int pflbm_get_stage_mode(const pflbm_domain* d);
+
+/* Time trial_steps steps of every stage mode on this domain's current state
+ * and keep the fastest (written to *mode_out if not NULL).  Trial steps write
+ * only the spare population buffer, so the state and step count are
+ * unchanged.  Synchronises the stream.  Errors: ESTATE before init, ECUDA. */
+pflbm_status pflbm_autotune(pflbm_domain* d, int trial_steps, int* mode_out);
+
+/* In PFLBM_STAGE_BOXES, stage interior tiles with TMA tensor loads (1, the
+ * default where the row pitch nx * element size is a multiple of 16 bytes)
+ * or fill every tile with cp.async / plain loads (0).  Both fill identical
+ * shared-memory boxes, so results are bitwise equal; the switch exists to
+ * test exactly that. */
 pflbm_status pflbm_set_tma(pflbm_domain* d, int enable);
 
 /* Steps taken since pflbm_init_phi. */

@@ -81,6 +81,7 @@ struct pflbm_domain {
   CUtensorMap tm_f[2], tm_h[2], tm_h0[2];
   int use_tma;  // maps built and usable
   int tma_off;  // caller asked for plain loads
+  int mode;     // StageMode of the step kernel
   int graphs;
   cudaGraphExec_t gexec;
   int g_parity;  // buffer parity the captured graph starts from
@@ -182,13 +183,17 @@ void build_maps(pflbm_domain* d) {
   d->use_tma = ok ? 1 : 0;
 }
 
-cudaError_t launch_step(const pflbm_domain* d, const StepArgs& a) {
+cudaError_t launch_step_mode(const pflbm_domain* d, int mode, const StepArgs& a) {
   const int form = d->par.force;
   switch (d->storage) {
-    case kFP32: return launch_step_fp32(form, a, d->stream);
-    case kFP16: return launch_step_fp16(form, a, d->stream);
-    default: return launch_step_bf16(form, a, d->stream);
+    case kFP32: return launch_step_fp32(form, mode, a, d->stream);
+    case kFP16: return launch_step_fp16(form, mode, a, d->stream);
+    default: return launch_step_bf16(form, mode, a, d->stream);
   }
+}
+
+cudaError_t launch_step(const pflbm_domain* d, const StepArgs& a) {
+  return launch_step_mode(d, d->mode, a);
 }
 
 void drop_graph(pflbm_domain* d) {
@@ -303,6 +308,7 @@ pflbm_status pflbm_create(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y, pflbm_st
   d->stream = (cudaStream_t)cuda_stream;
   d->ws = (char*)dev_workspace;
   d->lay = L;
+  d->mode = kGather;
   *out = d;
   return PFLBM_OK;
 }
@@ -403,6 +409,57 @@ pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
   d->t = 0;
   d->has_state = 1;
   drop_graph(d);
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode) {
+  if (!d || mode < 0 || mode >= kNumModes) return PFLBM_EINVAL;
+  d->mode = mode;
+  drop_graph(d);
+  return PFLBM_OK;
+}
+
+int pflbm_get_stage_mode(const pflbm_domain* d) { return d ? d->mode : -1; }
+
+pflbm_status pflbm_autotune(pflbm_domain* d, int trial_steps, int* mode_out) {
+  if (!d || trial_steps < 1) return PFLBM_EINVAL;
+  if (!d->has_state) {
+    set_msg("pflbm_autotune: no initial state");
+    return PFLBM_ESTATE;
+  }
+  // Trial steps read the current buffer and write the spare one without
+  // flipping buffers or writing (phi u) back, so the state is unchanged.
+  StepArgs a = make_args(d, d->cur);
+  a.first = d->t == 0;
+  a.macro = 0;
+  a.keep_phiu = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_mode = d->mode;
+  for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
+    e = launch_step_mode(d, m, a);  // warm-up (also sets kernel attributes)
+    if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
+    for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_step_mode(d, m, a);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, d->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      best_mode = m;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    set_err("autotune", e);
+    return PFLBM_ECUDA;
+  }
+  d->mode = best_mode;
+  drop_graph(d);
+  if (mode_out) *mode_out = best_mode;
   return PFLBM_OK;
 }
 

@@ -63,17 +63,22 @@ struct StepArgs {
   float* fields;      // macro mode: [kNFields][ny][nx]
   int first;          // first step of a run: d_t(phi u) = 0
   int macro;          // 1: write fields instead of colliding
+  int keep_phiu;      // 1: do not write (phi u)^t back (autotuning trial steps)
 };
 
 // Tile of the fused step kernel.
 constexpr int kTX = 32;
 constexpr int kTY = 16;
-constexpr int kThreads = 512;  // one node per thread in the collision pass
-// Box buffers per CTA: 2 = the next tile's loads fly during this tile's
-// compute (one CTA per SM); 1 = two CTAs per SM overlap each other's loads
-// and compute.
-constexpr int kBoxBuffers = 1;
-constexpr int kMinBlocks = kBoxBuffers == 1 ? 2 : 1;
+// How a tile gets the populations it pulls (the autotuner picks per domain):
+//   kBoxes   TMA box loads into shared memory (cp.async for seam tiles); a
+//            persistent grid of two 512-thread CTAs per SM, each walking tiles
+//   kGather  direct L1-cached gathers from global memory; one 256-thread CTA
+//            per tile, four CTAs per SM
+enum StageMode { kBoxes = 0, kGather = 1, kNumModes = 2 };
+constexpr int kThreadsBoxes = 512;
+constexpr int kThreadsGather = 256;
+constexpr int kBlocksBoxes = 2;   // CTAs per SM the box kernel is built for
+constexpr int kBlocksGather = 4;
 // Spin limit of the kernel's mbarrier waits (each try_wait suspends for a
 // hardware-bounded time); past it the kernel flags err and returns.
 constexpr long long kWaitLimit = 1ll << 20;
@@ -85,9 +90,9 @@ __host__ __device__ constexpr int box_w(int elem_bytes) { return kTX + 2 * box_x
 constexpr int kBoxRowsH = kTY + 6;  // phi is needed on the tile + 3 ring
 constexpr int kBoxRowsF = kTY + 2;  // f on the tile + 1 ring
 
-cudaError_t launch_step_fp32(int form, const StepArgs& a, cudaStream_t s);
-cudaError_t launch_step_fp16(int form, const StepArgs& a, cudaStream_t s);
-cudaError_t launch_step_bf16(int form, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp32(int form, int mode, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp16(int form, int mode, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_bf16(int form, int mode, const StepArgs& a, cudaStream_t s);
 
 // Initial state from phi0 (device, [ny][nx]).
 cudaError_t launch_init(int storage, const StepArgs& a, const float* phi0, cudaStream_t s);

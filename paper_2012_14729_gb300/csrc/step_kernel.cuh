@@ -1,22 +1,9 @@
 // Fused coupled step of the phase-field lattice Boltzmann method (Sec. 3 of
 // Zhang, Liang & Guo, arXiv 2012.14729) for sm_103a.
 //
-// A persistent kernel: one 512-thread CTA per SM walks a list of kTX x kTY
-// tiles and runs the whole time step for each.
-//
-// Staging.  The post-collision populations of the previous step are brought
-// into shared memory as one 2-D box per population plane: h planes on the
-// tile + 3 ring (rows) and f planes on the tile + 1 ring, each box shifted by
-// -c_i in y so that its rows hold the pulled values; in x every box spans the
-// same 16-byte aligned column range and the -c_ix shift is applied when the
-// box is read.  Interior tiles issue their 18 boxes as TMA tensor loads
-// (cp.async.bulk.tensor) completing on an mbarrier.  Two box buffers
-// alternate: while a CTA computes one tile, the TMA loads of its next tile
-// are in flight.  Tiles whose boxes wrap around the periodic seam or reach
-// the wall ghost rows fill the same boxes with plain loads.
-//
-// Passes over shared memory, recomputing the halo a tile's nodes need
-// instead of exchanging it through HBM:
+// A CTA runs the whole time step for kTX x kTY tiles of nodes, in passes over
+// shared memory that recompute the halo a tile's nodes need instead of
+// exchanging it through HBM:
 //   pass 1  phi = sum_i h_i on the tile + 3 ring (Eq. mac)
 //   pass 2  grad phi, lap phi (Eqs. ICS-1st, ICS-sec), mu (Eq.
 //           chemical_potential) and the form's level-1 fields on tile + 2
@@ -26,7 +13,19 @@
 //           with F_i and H_i (Eqs. fh, P_LBM, CH_LB_force), store of the
 //           post-collision populations; streaming is the next step's pull.
 // HBM traffic per node and step is the algorithmic state: 18 populations read
-// and written plus (phi u) read and written; halo re-reads hit L2.
+// and written plus (phi u) read and written; halo re-reads hit L1/L2.
+//
+// Two ways to obtain the pulled populations (StageMode, chosen per domain by
+// the autotuner):
+//   kBoxes   one 2-D box per population plane is staged in shared memory:
+//            h planes on the tile + 3 ring, f planes on the tile + 1 ring,
+//            each shifted by -c_i in y so that its rows hold pulled values; in
+//            x all boxes span the same 16-byte aligned columns and the -c_ix
+//            shift is applied on read.  Interior tiles issue the 18 boxes as
+//            TMA tensor loads (cp.async.bulk.tensor) on an mbarrier, seam and
+//            wall tiles fill them with cp.async; persistent CTAs walk tiles.
+//   kGather  every pulled value is an L1-cached load from the population
+//            planes; one CTA per tile.
 //
 // Walls (Sec. 4, half-way bounce-back): populations are stored with one
 // ghost row below and above the domain.  A node next to a wall writes the
@@ -41,7 +40,7 @@
 namespace pflbm {
 
 // ---------------------------------------------------------------------------
-// TMA and mbarrier (inline PTX)
+// TMA, cp.async and mbarrier (inline PTX)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -82,70 +81,179 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
       : "memory");
 }
+// 4-byte asynchronous copy global -> shared, zero-filled when !valid
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
-// ---------------------------------------------------------------------------
-// shared-memory geometry of one CTA
-// ---------------------------------------------------------------------------
 __host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; }
 
-template <class ST, int FORM>
-struct Smem {
+// ---------------------------------------------------------------------------
+// shared-memory geometry: per-tile fields, and the box set of kBoxes
+// ---------------------------------------------------------------------------
+template <int FORM>
+struct Fields {
+  static constexpr int B3X = kTX + 6, B3Y = kTY + 6;  // tile + 3 ring
+  static constexpr int B2X = kTX + 4, B2Y = kTY + 4;  // tile + 2 ring
+  static constexpr int B1X = kTX + 2, B1Y = kTY + 2;  // tile + 1 ring
+  static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
+  static constexpr int NE = extra_fields<FORM>();
+  static constexpr int OFF_PHI = 0;
+  static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
+  static constexpr int OFF_S1 = OFF_S2 + pad128((4 + NE) * N2 * 4);
+  static constexpr int BYTES = OFF_S1 + pad128(6 * N1 * 4);
+};
+
+template <class ST>
+struct Boxes {
   using T = typename ST::T;
   static constexpr int EB = sizeof(T);
   static constexpr int XPAD = box_xpad(EB);
   static constexpr int PW = box_w(EB);
   static constexpr int RH = kBoxRowsH, RF = kBoxRowsF;
-  // boxes: h planes (h_0 in float32 when the storage is split), f planes
+  // h planes (h_0 in float32 when the storage is split), then f planes
   static constexpr int HB0 = pad128(RH * PW * (ST::kSplitH0 ? 4 : EB));
   static constexpr int HB = pad128(RH * PW * EB);
   static constexpr int FB = pad128(RF * PW * EB);
-  static constexpr int BUF = HB0 + 8 * HB + 9 * FB;  // one set of 18 boxes
-  static constexpr int B3X = kTX + 6, B3Y = kTY + 6;
-  static constexpr int B2X = kTX + 4, B2Y = kTY + 4;
-  static constexpr int B1X = kTX + 2, B1Y = kTY + 2;
-  static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
-  static constexpr int NE = extra_fields<FORM>();
-  static constexpr int OFF_BAR = 0;        // two mbarriers
-  static constexpr int OFF_BUF = 128;      // two box buffers
-  static constexpr int OFF_PHI = OFF_BUF + kBoxBuffers * BUF;
-  static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
-  static constexpr int OFF_S1 = OFF_S2 + pad128((4 + NE) * N2 * 4);
-  static constexpr int BYTES = OFF_S1 + pad128(6 * N1 * 4);
+  static constexpr int BYTES = HB0 + 8 * HB + 9 * FB;
   static constexpr int TMA_TX = RH * PW * (ST::kSplitH0 ? 4 : EB) + 8 * RH * PW * EB +
                                 9 * RF * PW * EB;  // bytes the 18 loads deliver
-
   __device__ static int h_off(int i) { return i == 0 ? 0 : HB0 + (i - 1) * HB; }
   __device__ static int f_off(int i) { return HB0 + 8 * HB + i * FB; }
 };
 
-// population i of a box set at (row, col), decoded to float
-template <class ST, int I, class G>
-__device__ __forceinline__ float box_h(const unsigned char* bx, int r, int c, const Phys& P) {
-  if constexpr (ST::kSplitH0 && I == 0) {
-    return reinterpret_cast<const float*>(bx + G::h_off(0))[r * G::PW + c];
-  } else {
-    const typename ST::T v =
-        reinterpret_cast<const typename ST::T*>(bx + G::h_off(I))[r * G::PW + c];
-    return ST::dec(v, qw(I) * P.inv_sh);
+// ---------------------------------------------------------------------------
+// sources of pulled populations
+// ---------------------------------------------------------------------------
+// From the shared-memory box set bx.  Ring-3 node (r, cc) of pass 1, ring-1
+// node (ly, lx) of pass 3 and tile node (ly, lx) of pass 4; the population i
+// pulled at a node sits at box column (node column - c_ix) of its row.
+template <class ST>
+struct BoxSrc {
+  using G = Boxes<ST>;
+  const unsigned char* bx;
+  template <int I>
+  __device__ __forceinline__ float h(int r, int c, const Phys& P) const {
+    if constexpr (ST::kSplitH0 && I == 0) {
+      return reinterpret_cast<const float*>(bx + G::h_off(0))[r * G::PW + c];
+    } else {
+      const typename ST::T v =
+          reinterpret_cast<const typename ST::T*>(bx + G::h_off(I))[r * G::PW + c];
+      return ST::dec(v, qw(I) * P.inv_sh);
+    }
   }
-}
-template <class ST, int I, class G>
-__device__ __forceinline__ float box_f(const unsigned char* bx, int r, int c, const Phys& P) {
-  const typename ST::T v = reinterpret_cast<const typename ST::T*>(bx + G::f_off(I))[r * G::PW + c];
-  return ST::dec(v, qw(I) * P.inv_sf);
-}
+  template <int I>
+  __device__ __forceinline__ float f(int r, int c, const Phys& P) const {
+    const typename ST::T v =
+        reinterpret_cast<const typename ST::T*>(bx + G::f_off(I))[r * G::PW + c];
+    return ST::dec(v, qw(I) * P.inv_sf);
+  }
+  __device__ __forceinline__ float phi(const StepArgs& a, int r, int cc, int, int) const {
+    const int c = cc + G::XPAD - 3;
+    const Phys& P = a.p;
+    float s = h<0>(r, c, P);
+    s += h<1>(r, c - 1, P);
+    s += h<2>(r, c, P);
+    s += h<3>(r, c + 1, P);
+    s += h<4>(r, c, P);
+    s += h<5>(r, c - 1, P);
+    s += h<6>(r, c + 1, P);
+    s += h<7>(r, c + 1, P);
+    s += h<8>(r, c - 1, P);
+    return s;
+  }
+  __device__ __forceinline__ void f_ring1(const StepArgs& a, int ly, int lx, int, int,
+                                          float* f) const {
+    const int c = lx + G::XPAD - 1;
+    const Phys& P = a.p;
+    f[1] = this->f<1>(ly, c - 1, P);
+    f[2] = this->f<2>(ly, c, P);
+    f[3] = this->f<3>(ly, c + 1, P);
+    f[4] = this->f<4>(ly, c, P);
+    f[5] = this->f<5>(ly, c - 1, P);
+    f[6] = this->f<6>(ly, c + 1, P);
+    f[7] = this->f<7>(ly, c + 1, P);
+    f[8] = this->f<8>(ly, c - 1, P);
+  }
+  __device__ __forceinline__ void f_node(const StepArgs& a, int ly, int lx, int, int,
+                                         float* f) const {
+    const int c = lx + G::XPAD, r = ly + 1;
+    const Phys& P = a.p;
+    f[0] = this->f<0>(r, c, P);
+    f[1] = this->f<1>(r, c - 1, P);
+    f[2] = this->f<2>(r, c, P);
+    f[3] = this->f<3>(r, c + 1, P);
+    f[4] = this->f<4>(r, c, P);
+    f[5] = this->f<5>(r, c - 1, P);
+    f[6] = this->f<6>(r, c + 1, P);
+    f[7] = this->f<7>(r, c + 1, P);
+    f[8] = this->f<8>(r, c - 1, P);
+  }
+  __device__ __forceinline__ void h_node(const StepArgs& a, int ly, int lx, int, int,
+                                         float* hh) const {
+    const int c = lx + G::XPAD, r = ly + 3;
+    const Phys& P = a.p;
+    hh[0] = h<0>(r, c, P);
+    hh[1] = h<1>(r, c - 1, P);
+    hh[2] = h<2>(r, c, P);
+    hh[3] = h<3>(r, c + 1, P);
+    hh[4] = h<4>(r, c, P);
+    hh[5] = h<5>(r, c - 1, P);
+    hh[6] = h<6>(r, c + 1, P);
+    hh[7] = h<7>(r, c + 1, P);
+    hh[8] = h<8>(r, c - 1, P);
+  }
+};
 
+// Straight from the population planes (global coordinates of the node).
+template <class ST>
+struct GatherSrc {
+  __device__ __forceinline__ float phi(const StepArgs& a, int, int, int gx, int gy) const {
+    return pull_phi<ST>(a, pull_idx(a.L, gx, gy));
+  }
+  __device__ __forceinline__ void f_ring1(const StepArgs& a, int, int, int gx, int gy,
+                                          float* f) const {
+    const Pull q = pull_idx(a.L, gx, gy);
+    f[1] = load_f<ST, 1>(a, q.i[1]);
+    f[2] = load_f<ST, 2>(a, q.i[2]);
+    f[3] = load_f<ST, 3>(a, q.i[3]);
+    f[4] = load_f<ST, 4>(a, q.i[4]);
+    f[5] = load_f<ST, 5>(a, q.i[5]);
+    f[6] = load_f<ST, 6>(a, q.i[6]);
+    f[7] = load_f<ST, 7>(a, q.i[7]);
+    f[8] = load_f<ST, 8>(a, q.i[8]);
+  }
+  __device__ __forceinline__ void f_node(const StepArgs& a, int, int, int gx, int gy,
+                                         float* f) const {
+    pull_f<ST>(a, pull_idx(a.L, gx, gy), f);
+  }
+  __device__ __forceinline__ void h_node(const StepArgs& a, int, int, int gx, int gy,
+                                         float* h) const {
+    pull_h<ST>(a, pull_idx(a.L, gx, gy), h);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// box staging
+// ---------------------------------------------------------------------------
 // Tiles whose 18 boxes lie inside the stored planes without wrapping.
-template <class G>
+template <class ST>
 __device__ __forceinline__ bool tma_tile(const StepArgs& a, int x0, int y0) {
+  using G = Boxes<ST>;
   return a.use_tma && x0 - G::XPAD >= 0 && x0 + kTX + G::XPAD <= a.L.nx && y0 >= 4 &&
          y0 + kTY + 4 <= a.L.ny;
 }
 
 // Issue the 18 box loads of the tile at (x0, y0) into box set bx (one thread).
-template <class ST, class G>
+template <class ST>
 __device__ __forceinline__ void issue_tma(const StepArgs& a, unsigned char* bx, uint64_t* bar,
                                           int x0, int y0) {
+  using G = Boxes<ST>;
   fence_proxy_async_smem();
   mbar_arrive_expect_tx(bar, G::TMA_TX);
   const int xs = x0 - G::XPAD;
@@ -161,88 +269,54 @@ __device__ __forceinline__ void issue_tma(const StepArgs& a, unsigned char* bx, 
   }
 }
 
-// Fill the boxes with plain loads (tiles at the periodic seam or the walls).
-// Box row r of plane i holds storage row (node row - c_iy) + 1 of the rows
-// the tile needs; rows the tile never pulls (beyond a wall) are zero.
-template <class ST, class G>
-__device__ void fill_boxes_plain(const StepArgs& a, unsigned char* bx, int x0, int y0) {
+// storage row of source domain row yy, or -1 beyond a wall's ghost row
+__device__ __forceinline__ int source_row(const Lattice& L, int yy) {
+  if (L.wall) return (yy >= -1 && yy <= L.ny) ? yy + 1 : -1;
+  return wrap(yy, L.ny) + 1;
+}
+
+// Fill the boxes of a seam or wall tile.  Box row r of plane i holds storage
+// row (node row - c_iy) + 1 of the rows the tile needs; rows the tile never
+// pulls (beyond a wall) are zero.  ASYNC (4-byte storage): cp.async per
+// element, completed by cp_async_wait_all() and a CTA barrier; otherwise
+// plain loads and stores.
+template <class ST, int NT, bool ASYNC>
+__device__ void fill_boxes(const StepArgs& a, unsigned char* bx, int x0, int y0) {
+  using G = Boxes<ST>;
   using T = typename ST::T;
   const Lattice& L = a.L;
-  auto srow = [&](int yy) -> int {  // storage row of source domain row yy, or -1
-    if (L.wall) return (yy >= -1 && yy <= L.ny) ? yy + 1 : -1;
-    return wrap(yy, L.ny) + 1;
-  };
-  for (int e = threadIdx.x; e < G::RH * G::PW; e += kThreads) {
+  for (int e = threadIdx.x; e < G::RH * G::PW; e += NT) {
     const int r = e / G::PW, c = e - r * G::PW;
     const int gx = wrap(x0 - G::XPAD + c, L.nx);
     const int yn = y0 - 3 + r;  // node row
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const int sr = srow(yn - qcy(i));
+      const int sr = source_row(L, yn - qcy(i));
+      const int off = sr >= 0 ? sr * L.nx + gx : 0;
       if (ST::kSplitH0 && i == 0) {
-        reinterpret_cast<float*>(bx + G::h_off(0))[e] = sr >= 0 ? a.h0_in[sr * L.nx + gx] : 0.0f;
+        float* d = reinterpret_cast<float*>(bx + G::h_off(0)) + e;
+        *d = sr >= 0 ? a.h0_in[off] : 0.0f;
       } else {
         const int pl = ST::kSplitH0 ? i - 1 : i;
-        const T* src = reinterpret_cast<const T*>(a.h_in) + (size_t)pl * L.plane;
-        reinterpret_cast<T*>(bx + G::h_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
+        const T* src = reinterpret_cast<const T*>(a.h_in) + (size_t)pl * L.plane + off;
+        T* d = reinterpret_cast<T*>(bx + G::h_off(i)) + e;
+        if constexpr (ASYNC) cp_async4(d, src, sr >= 0);
+        else *d = sr >= 0 ? *src : T(0.0f);
       }
     }
   }
-  for (int e = threadIdx.x; e < G::RF * G::PW; e += kThreads) {
+  for (int e = threadIdx.x; e < G::RF * G::PW; e += NT) {
     const int r = e / G::PW, c = e - r * G::PW;
     const int gx = wrap(x0 - G::XPAD + c, L.nx);
     const int yn = y0 - 1 + r;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      const int sr = srow(yn - qcy(i));
-      const T* src = reinterpret_cast<const T*>(a.f_in) + (size_t)i * L.plane;
-      reinterpret_cast<T*>(bx + G::f_off(i))[e] = sr >= 0 ? src[sr * L.nx + gx] : T(0.0f);
-    }
-  }
-}
-
-// Asynchronous version of fill_boxes_plain for 4-byte storage: each element
-// is one cp.async (zero-filled when the source row is beyond a wall), so
-// seam and wall tiles are prefetched like TMA tiles.  Completion: each
-// thread's cp.async.wait_all, then a CTA barrier.
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
-               "r"(valid ? 4 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-template <class ST, class G>
-__device__ void fill_boxes_async(const StepArgs& a, unsigned char* bx, int x0, int y0) {
-  static_assert(sizeof(typename ST::T) == 4, "cp.async path is for 4-byte storage");
-  const Lattice& L = a.L;
-  auto srow = [&](int yy) -> int {
-    if (L.wall) return (yy >= -1 && yy <= L.ny) ? yy + 1 : -1;
-    return wrap(yy, L.ny) + 1;
-  };
-  const float* hin = reinterpret_cast<const float*>(a.h_in);
-  const float* fin = reinterpret_cast<const float*>(a.f_in);
-  for (int e = threadIdx.x; e < G::RH * G::PW; e += kThreads) {
-    const int r = e / G::PW, c = e - r * G::PW;
-    const int gx = wrap(x0 - G::XPAD + c, L.nx);
-    const int yn = y0 - 3 + r;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int sr = srow(yn - qcy(i));
-      const float* src = hin + (size_t)i * L.plane + (sr >= 0 ? sr * L.nx + gx : 0);
-      cp_async4(reinterpret_cast<float*>(bx + G::h_off(i)) + e, src, sr >= 0);
-    }
-  }
-  for (int e = threadIdx.x; e < G::RF * G::PW; e += kThreads) {
-    const int r = e / G::PW, c = e - r * G::PW;
-    const int gx = wrap(x0 - G::XPAD + c, L.nx);
-    const int yn = y0 - 1 + r;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int sr = srow(yn - qcy(i));
-      const float* src = fin + (size_t)i * L.plane + (sr >= 0 ? sr * L.nx + gx : 0);
-      cp_async4(reinterpret_cast<float*>(bx + G::f_off(i)) + e, src, sr >= 0);
+      const int sr = source_row(L, yn - qcy(i));
+      const T* src = reinterpret_cast<const T*>(a.f_in) + (size_t)i * L.plane +
+                     (sr >= 0 ? sr * L.nx + gx : 0);
+      T* d = reinterpret_cast<T*>(bx + G::f_off(i)) + e;
+      if constexpr (ASYNC) cp_async4(d, src, sr >= 0);
+      else *d = sr >= 0 ? *src : T(0.0f);
     }
   }
 }
@@ -266,9 +340,11 @@ __device__ __forceinline__ bool wait_boxes(const StepArgs& a, uint64_t* bar, uin
   return true;
 }
 
-// One collision of an opposite pair (i, j) with c_j = -c_i, w_j = w_i:
+// ---------------------------------------------------------------------------
+// collision of an opposite pair (i, j) with c_j = -c_i, w_j = w_i:
 // f_i^+ = f_i (1 - 1/tau_f) + f_i^eq / tau_f + (1 - 1/(2 tau_f)) F_i and the
-// same for h with tau_h and H_i (Eqs. fh, P_LBM, CH_LB_force, heq_CH).
+// same for h with tau_h and H_i (Eqs. fh, P_LBM, CH_LB_force, heq_CH)
+// ---------------------------------------------------------------------------
 struct CollideConsts {
   float ux, uy, Pr, rho3, uu15, Fx, Fy, uF, rx, ry, uR, omf, omf1, cff;
   float phi3, emu, A, dtx, dty, omh, omh1, chh;
@@ -300,70 +376,64 @@ __device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, f
 }
 
 // ---------------------------------------------------------------------------
-// one tile: passes 1-4 from the box set bx
+// one tile: passes 1-4, populations from SRC, fields in shared memory fs
 // ---------------------------------------------------------------------------
-template <int FORM, class ST>
-__device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char* bx,
-                                          unsigned char* sm, int x0, int y0) {
-  using G = Smem<ST, FORM>;
-  constexpr int B3X = G::B3X, B2X = G::B2X, B1X = G::B1X, B1Y = G::B1Y;
-  constexpr int N2 = G::N2, N1 = G::N1;
-  constexpr int XP = G::XPAD;
+template <int FORM, class ST, int NT, class SRC>
+__device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, unsigned char* fs,
+                                          int x0, int y0) {
+  using F = Fields<FORM>;
+  constexpr int B3X = F::B3X, B2X = F::B2X, B1X = F::B1X, B1Y = F::B1Y;
+  constexpr int N2 = F::N2, N1 = F::N1;
+  constexpr int NPT = kTX * kTY / NT;  // collision nodes per thread
+  static_assert(kTX * kTY % NT == 0, "whole collision nodes per thread");
   // level-1 field slots in s2, ring-1 slots in s1
   constexpr int GX = 0, GY = 1, LAP = 2, MU = 3, E0 = 4;
   constexpr int FX = 0, FY = 1, UX = 2, UY = 3, PUX = 4, PUY = 5;
-  float* sPhi = reinterpret_cast<float*>(sm + G::OFF_PHI);
-  float* s2 = reinterpret_cast<float*>(sm + G::OFF_S2);
-  float* s1 = reinterpret_cast<float*>(sm + G::OFF_S1);
+  float* sPhi = reinterpret_cast<float*>(fs + F::OFF_PHI);
+  float* s2 = reinterpret_cast<float*>(fs + F::OFF_S2);
+  float* s1 = reinterpret_cast<float*>(fs + F::OFF_S1);
   const Lattice& L = a.L;
   const Phys& P = a.p;
   const int tid = threadIdx.x;
-  static_assert(kTX * kTY == kThreads, "one collision node per thread");
-
-  // (phi u)^{t-1} of this thread's collision node, loaded first so that the
-  // load latency overlaps passes 1-3
   const int nn = L.nx * L.ny;
-  float pu_prev_x = 0.0f, pu_prev_y = 0.0f;
-  {
-    const int gx = x0 + tid % kTX, gy = y0 + tid / kTX;
+
+  // (phi u)^{t-1} of this thread's collision nodes, loaded first so that the
+  // load latency overlaps passes 1-3
+  float pu_prev_x[NPT], pu_prev_y[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int k = tid + j * NT;
+    const int gx = x0 + k % kTX, gy = y0 + k / kTX;
+    pu_prev_x[j] = 0.0f;
+    pu_prev_y[j] = 0.0f;
     if (!a.first && !a.macro && gx < L.nx && gy < L.ny) {
-      pu_prev_x = a.phiu[gy * L.nx + gx];
-      pu_prev_y = a.phiu[nn + gy * L.nx + gx];
+      pu_prev_x[j] = a.phiu[gy * L.nx + gx];
+      pu_prev_y[j] = a.phiu[nn + gy * L.nx + gx];
     }
   }
 
   // ---- pass 1: phi on tile + 3 ------------------------------------------------
-  for (int k = tid; k < G::N3; k += kThreads) {
+  for (int k = tid; k < F::N3; k += NT) {
     const int r = k / B3X, cc = k - r * B3X;
     const int yn = y0 - 3 + r;
     if (L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
-    const int c = cc + XP - 3;
-    float s = box_h<ST, 0, G>(bx, r, c, P);
-    s += box_h<ST, 1, G>(bx, r, c - 1, P);
-    s += box_h<ST, 2, G>(bx, r, c, P);
-    s += box_h<ST, 3, G>(bx, r, c + 1, P);
-    s += box_h<ST, 4, G>(bx, r, c, P);
-    s += box_h<ST, 5, G>(bx, r, c - 1, P);
-    s += box_h<ST, 6, G>(bx, r, c + 1, P);
-    s += box_h<ST, 7, G>(bx, r, c + 1, P);
-    s += box_h<ST, 8, G>(bx, r, c - 1, P);
-    sPhi[k] = s;
+    sPhi[k] = src.phi(a, r, cc, wrap(x0 - 3 + cc, L.nx), L.wall ? yn : wrap(yn, L.ny));
   }
   __syncthreads();
   if (L.wall && (y0 - 3 < 0 || y0 + kTY + 3 > L.ny)) {
     // mirror ghosts of phi about the wall planes
-    for (int k = tid; k < G::N3; k += kThreads) {
+    for (int k = tid; k < F::N3; k += NT) {
       const int r = k / B3X, cc = k - r * B3X;
       const int yn = y0 - 3 + r;
       if (yn >= 0 && yn < L.ny) continue;
       const int rm = map_row(yn, L.ny, 1) - (y0 - 3);
-      sPhi[k] = (rm >= 0 && rm < G::B3Y) ? sPhi[rm * B3X + cc] : 0.0f;
+      sPhi[k] = (rm >= 0 && rm < F::B3Y) ? sPhi[rm * B3X + cc] : 0.0f;
     }
     __syncthreads();
   }
 
   // ---- pass 2: grad phi, lap phi, mu, level-1 fields on tile + 2 -------------
-  for (int k = tid; k < N2; k += kThreads) {
+  for (int k = tid; k < N2; k += NT) {
     const int ly = k / B2X, lx = k - ly * B2X;
     const int c = (ly + 1) * B3X + lx + 1;
     const float pc = sPhi[c];
@@ -392,7 +462,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
   __syncthreads();
 
   // ---- pass 3: force, rho, u, phi u on tile + 1 -----------------------------
-  for (int k = tid; k < N1; k += kThreads) {
+  for (int k = tid; k < N1; k += NT) {
     const int ly = k / B1X, lx = k - ly * B1X;
     const int c2 = (ly + 1) * B2X + lx + 1;
     const float phi = sPhi[(ly + 2) * B3X + lx + 2];
@@ -436,14 +506,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
     const float rho = P.rho_mid + P.drho_half * phi;
     Fx += (rho - P.rho0) * P.gx;
     Fy += (rho - P.rho0) * P.gy;
-    // pulled f from the boxes: row ly, column (lx - 1) + XP - c_ix
-    const int c = lx + XP - 1;
-    const float f1 = box_f<ST, 1, G>(bx, ly, c - 1, P), f2 = box_f<ST, 2, G>(bx, ly, c, P);
-    const float f3 = box_f<ST, 3, G>(bx, ly, c + 1, P), f4 = box_f<ST, 4, G>(bx, ly, c, P);
-    const float f5 = box_f<ST, 5, G>(bx, ly, c - 1, P), f6 = box_f<ST, 6, G>(bx, ly, c + 1, P);
-    const float f7 = box_f<ST, 7, G>(bx, ly, c + 1, P), f8 = box_f<ST, 8, G>(bx, ly, c - 1, P);
-    const float jx = (f1 - f3) + ((f5 - f6) + (f8 - f7));
-    const float jy = (f2 - f4) + ((f5 - f8) + (f6 - f7));
+    float f[9];
+    src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
+    const float jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    const float jy = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
     // Eq. mac: u = [sum c f + cs^2 F / 2] / (cs^2 rho)
     const float irho = __fdividef(1.0f, rho);
     const float ux = (3.0f * jx + 0.5f * Fx) * irho;
@@ -464,7 +530,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
     const bool bot = lb >= 0 && lb + 1 < B1Y;
     const bool top = lt - 1 >= 0 && lt < B1Y;
     if (bot || top) {
-      for (int lx = tid; lx < B1X; lx += kThreads) {
+      for (int lx = tid; lx < B1X; lx += NT) {
         if (bot) {
           const int g = lb * B1X + lx, m = (lb + 1) * B1X + lx;
           const float pm = sPhi[(lb + 1 + 2) * B3X + lx + 2];
@@ -483,7 +549,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
   }
 
   // ---- pass 4: collide and store on the tile --------------------------------
-  for (int k = tid; k < kTX * kTY; k += kThreads) {
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int k = tid + j * NT;
     const int ly = k / kTX, lx = k - ly * kTX;
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx >= L.nx || gy >= L.ny) continue;
@@ -497,18 +565,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
     const float rho = P.rho_mid + P.drho_half * phi;
     const float drx = P.drho_half * Gx, dry = P.drho_half * Gy;
 
-    // pulled populations: f box row ly + 1, h box row ly + 3, column lx + XP - c_ix
-    const int c = lx + XP;
-    const float f0 = box_f<ST, 0, G>(bx, ly + 1, c, P);
-    const float f1 = box_f<ST, 1, G>(bx, ly + 1, c - 1, P);
-    const float f2 = box_f<ST, 2, G>(bx, ly + 1, c, P);
-    const float f3 = box_f<ST, 3, G>(bx, ly + 1, c + 1, P);
-    const float f4 = box_f<ST, 4, G>(bx, ly + 1, c, P);
-    const float f5 = box_f<ST, 5, G>(bx, ly + 1, c - 1, P);
-    const float f6 = box_f<ST, 6, G>(bx, ly + 1, c + 1, P);
-    const float f7 = box_f<ST, 7, G>(bx, ly + 1, c + 1, P);
-    const float f8 = box_f<ST, 8, G>(bx, ly + 1, c - 1, P);
-    const float sumf = f0 + (f1 + f2 + f3 + f4) + (f5 + f6 + f7 + f8);
+    float f[9];
+    src.f_node(a, ly, lx, gx, gy, f);
+    const float sumf = f[0] + (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
     // Eq. mac: P = sum f + cs^2/2 u . grad rho
     const float Pr = sumf + (ux * drx + uy * dry) * (1.0f / 6.0f);
     // div(phi u) by Eq. ICS-1st on the ring-1 values
@@ -517,8 +576,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
     const float pux = phi * ux, puy = phi * uy;
     float dtx = 0.0f, dty = 0.0f;
     if (!a.first) {
-      dtx = pux - pu_prev_x;
-      dty = puy - pu_prev_y;
+      dtx = pux - pu_prev_x[j];
+      dty = puy - pu_prev_y[j];
     }
 
     if (a.macro) {
@@ -543,20 +602,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
       o[8 * nn] = Fy;
       continue;
     }
-    a.phiu[n_idx] = pux;
-    a.phiu[nn + n_idx] = puy;
+    if (!a.keep_phiu) {
+      a.phiu[n_idx] = pux;
+      a.phiu[nn + n_idx] = puy;
+    }
 
-    const float h0 = box_h<ST, 0, G>(bx, ly + 3, c, P);
-    const float h1 = box_h<ST, 1, G>(bx, ly + 3, c - 1, P);
-    const float h2 = box_h<ST, 2, G>(bx, ly + 3, c, P);
-    const float h3 = box_h<ST, 3, G>(bx, ly + 3, c + 1, P);
-    const float h4 = box_h<ST, 4, G>(bx, ly + 3, c, P);
-    const float h5 = box_h<ST, 5, G>(bx, ly + 3, c - 1, P);
-    const float h6 = box_h<ST, 6, G>(bx, ly + 3, c + 1, P);
-    const float h7 = box_h<ST, 7, G>(bx, ly + 3, c + 1, P);
-    const float h8 = box_h<ST, 8, G>(bx, ly + 3, c - 1, P);
+    float h[9];
+    src.h_node(a, ly, lx, gx, gy, h);
 
-    // relaxation constants: tau_f = 1/2 + mu(phi) / (cs^2 rho) (Sec. 3)
+    // relaxation: tau_f = 1/2 + mu(phi) / (cs^2 rho) (Sec. 3)
     const float mv = P.mu_mid + P.mu_dhalf * phi;
     const float omf = __fdividef(1.0f, 0.5f + 3.0f * mv * __fdividef(1.0f, rho));
     CollideConsts K;
@@ -590,14 +644,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
       const float s0 = -K.uu15;
       const float feq0 = w0 * (Pr + K.rho3 * s0);
       const float F0 = w0 * ((1.0f + s0) * (-K.uF) + s0 * (-K.uR));
-      fo[0] = f0 * K.omf1 + feq0 * omf + K.cff * F0;
+      fo[0] = f[0] * K.omf1 + feq0 * omf + K.cff * F0;
       const float heq0 = phi + (w0 - 1.0f) * K.emu;
-      ho[0] = h0 * K.omh1 + heq0 * K.omh + K.chh * ((w0 - 1.0f) * K.A);
+      ho[0] = h[0] * K.omh1 + heq0 * K.omh + K.chh * ((w0 - 1.0f) * K.A);
     }
-    collide_pair<1>(K, f1, f3, h1, h3, fo[1], fo[3], ho[1], ho[3]);
-    collide_pair<2>(K, f2, f4, h2, h4, fo[2], fo[4], ho[2], ho[4]);
-    collide_pair<5>(K, f5, f7, h5, h7, fo[5], fo[7], ho[5], ho[7]);
-    collide_pair<6>(K, f6, f8, h6, h8, fo[6], fo[8], ho[6], ho[8]);
+    collide_pair<1>(K, f[1], f[3], h[1], h[3], fo[1], fo[3], ho[1], ho[3]);
+    collide_pair<2>(K, f[2], f[4], h[2], h[4], fo[2], fo[4], ho[2], ho[4]);
+    collide_pair<5>(K, f[5], f[7], h[5], h[7], fo[5], fo[7], ho[5], ho[7]);
+    collide_pair<6>(K, f[6], f[8], h[6], h[8], fo[6], fo[8], ho[6], ho[8]);
 
     const int o = (gy + 1) * L.nx + gx;
     store_f<ST, 0>(a, o, fo[0]); store_h<ST, 0>(a, o, ho[0]);
@@ -645,124 +699,96 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const unsigned char
 }
 
 // ---------------------------------------------------------------------------
-// the persistent step kernel
+// kernels
 // ---------------------------------------------------------------------------
+// kBoxes: persistent CTAs, each walking tiles t = blockIdx.x + k gridDim.x;
+// the box set of the next tile is staged when the current one is done (two
+// CTAs per SM overlap one another's staging and compute).
 template <int FORM, class ST>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_step(const __grid_constant__ StepArgs a) {
-  using G = Smem<ST, FORM>;
+__global__ void __launch_bounds__(kThreadsBoxes, kBlocksBoxes)
+    k_step_boxes(const __grid_constant__ StepArgs a) {
+  using G = Boxes<ST>;
+  constexpr int NT = kThreadsBoxes;
+  constexpr bool kAsync = sizeof(typename ST::T) == 4;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + G::OFF_BAR);
-  unsigned char* bufs = sm + G::OFF_BUF;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
+  unsigned char* bx = sm + 128;
+  unsigned char* fs = bx + G::BYTES;
 
   const int ntx = (a.L.nx + kTX - 1) / kTX;
   const int ntiles = ntx * ((a.L.ny + kTY - 1) / kTY);
   int t = blockIdx.x;
   if (t >= ntiles) return;
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-
-  // seam and wall tiles of 4-byte storage are prefetched with cp.async;
-  // for 16-bit storage they are filled synchronously before use
-  constexpr bool kAsyncFill = sizeof(typename ST::T) == 4;
   uint32_t parity = 0u;
-  int buf = 0;
-  int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
-  bool tma_cur = tma_tile<G>(a, x0, y0);
-  if (tma_cur) {
-    if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs, &bars[0], x0, y0);
-  } else if constexpr (kAsyncFill) {
-    fill_boxes_async<ST, G>(a, bufs, x0, y0);
-  } else {
-    fill_boxes_plain<ST, G>(a, bufs, x0, y0);
-    __syncthreads();
-  }
-
-  for (;;) {
-    unsigned char* bx = bufs + buf * G::BUF;
-    if (tma_cur) {
-      // phase parity of each buffer's barrier, kept in two bits of `parity`
-      if (!wait_boxes(a, &bars[buf], (parity >> buf) & 1u)) return;
-      parity ^= 1u << buf;
-    } else if constexpr (kAsyncFill) {
-      cp_async_wait_all();
+  const BoxSrc<ST> src{bx};
+  for (; t < ntiles; t += gridDim.x) {
+    const int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
+    if (tma_tile<ST>(a, x0, y0)) {
+      if (threadIdx.x == 0) issue_tma<ST>(a, bx, bar, x0, y0);
+      if (!wait_boxes(a, bar, parity)) return;
+      parity ^= 1u;
+    } else {
+      fill_boxes<ST, NT, kAsync>(a, bx, x0, y0);
+      if constexpr (kAsync) cp_async_wait_all();
       __syncthreads();
     }
-    const int tn = t + gridDim.x;
-    const int xn = (tn % ntx) * kTX, yn = (tn / ntx) * kTY;
-    const bool tma_next = tn < ntiles && tma_tile<G>(a, xn, yn);
-    const int nb = kBoxBuffers == 2 ? buf ^ 1 : 0;  // buffer of the next tile
-    if constexpr (kBoxBuffers == 2) {
-      // prefetch the next tile into the other buffer (its last reader, the
-      // tile before this one, finished at the barrier closing that tile)
-      if (tma_next) {
-        if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs + nb * G::BUF, &bars[nb], xn, yn);
-      } else if constexpr (kAsyncFill) {
-        if (tn < ntiles) fill_boxes_async<ST, G>(a, bufs + nb * G::BUF, xn, yn);
-      }
-    }
-
-    step_tile<FORM, ST>(a, bx, sm, x0, y0);
+    step_tile<FORM, ST, NT>(a, src, fs, x0, y0);
     __syncthreads();
-
-    if (tn >= ntiles) break;
-    if constexpr (kBoxBuffers == 1) {
-      // single buffer: stage the next tile now that this one is done
-      if (tma_next) {
-        if (threadIdx.x == 0) issue_tma<ST, G>(a, bufs, &bars[0], xn, yn);
-      } else if constexpr (kAsyncFill) {
-        fill_boxes_async<ST, G>(a, bufs, xn, yn);
-      } else {
-        fill_boxes_plain<ST, G>(a, bufs, xn, yn);
-        __syncthreads();
-      }
-    } else if constexpr (!kAsyncFill) {
-      if (!tma_next) {
-        fill_boxes_plain<ST, G>(a, bufs + nb * G::BUF, xn, yn);
-        __syncthreads();
-      }
-    }
-    t = tn;
-    x0 = xn;
-    y0 = yn;
-    tma_cur = tma_next;
-    buf = nb;
   }
+}
+
+// kGather: one CTA per tile, populations gathered through L1.
+template <int FORM, class ST>
+__global__ void __launch_bounds__(kThreadsGather, kBlocksGather)
+    k_step_gather(const __grid_constant__ StepArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int ntx = (a.L.nx + kTX - 1) / kTX;
+  const int x0 = (blockIdx.x % ntx) * kTX, y0 = (blockIdx.x / ntx) * kTY;
+  step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST>{}, sm, x0, y0);
 }
 
 int num_sms();
 
 template <int FORM, class ST>
-cudaError_t launch_form(const StepArgs& a, cudaStream_t s) {
-  using G = Smem<ST, FORM>;
-  static bool configured = false;  // per instantiation; attribute is per device function
+cudaError_t launch_form(int mode, const StepArgs& a, cudaStream_t s) {
+  static bool configured = false;  // per instantiation; attributes are per function
+  constexpr int kBoxBytes = 128 + Boxes<ST>::BYTES + Fields<FORM>::BYTES;
+  constexpr int kGatherBytes = Fields<FORM>::BYTES;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step<FORM, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_step_boxes<FORM, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step_gather<FORM, ST>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, kGatherBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const int ntiles = ((a.L.nx + kTX - 1) / kTX) * ((a.L.ny + kTY - 1) / kTY);
-  const int slots = num_sms() * kMinBlocks;
-  const int grid = ntiles < slots ? ntiles : slots;
-  k_step<FORM, ST><<<grid, kThreads, G::BYTES, s>>>(a);
+  if (mode == kBoxes) {
+    const int slots = num_sms() * kBlocksBoxes;
+    k_step_boxes<FORM, ST><<<ntiles < slots ? ntiles : slots, kThreadsBoxes, kBoxBytes, s>>>(a);
+  } else {
+    k_step_gather<FORM, ST><<<ntiles, kThreadsGather, kGatherBytes, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <class ST>
-cudaError_t launch_step_impl(int form, const StepArgs& a, cudaStream_t s) {
+cudaError_t launch_step_impl(int form, int mode, const StepArgs& a, cudaStream_t s) {
   switch (form) {
-    case kSTF1: return launch_form<kSTF1, ST>(a, s);
-    case kSTF2: return launch_form<kSTF2, ST>(a, s);
-    case kCPF1: return launch_form<kCPF1, ST>(a, s);
-    case kCPF2: return launch_form<kCPF2, ST>(a, s);
-    case kPF1: return launch_form<kPF1, ST>(a, s);
-    case kPF2: return launch_form<kPF2, ST>(a, s);
-    case kCSF1: return launch_form<kCSF1, ST>(a, s);
-    case kCSF2: return launch_form<kCSF2, ST>(a, s);
+    case kSTF1: return launch_form<kSTF1, ST>(mode, a, s);
+    case kSTF2: return launch_form<kSTF2, ST>(mode, a, s);
+    case kCPF1: return launch_form<kCPF1, ST>(mode, a, s);
+    case kCPF2: return launch_form<kCPF2, ST>(mode, a, s);
+    case kPF1: return launch_form<kPF1, ST>(mode, a, s);
+    case kPF2: return launch_form<kPF2, ST>(mode, a, s);
+    case kCSF1: return launch_form<kCSF1, ST>(mode, a, s);
+    case kCSF2: return launch_form<kCSF2, ST>(mode, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -71,6 +71,9 @@ SIGNATURES = {
     "pflbm_step": (_i, [_vp, _i]),
     "pflbm_set_graphs": (_i, [_vp, _i]),
     "pflbm_set_tma": (_i, [_vp, _i]),
+    "pflbm_set_stage_mode": (_i, [_vp, _i]),
+    "pflbm_get_stage_mode": (_i, [_vp]),
+    "pflbm_autotune": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "pflbm_steps_done": (ctypes.c_longlong, [_vp]),
     "pflbm_read": (_i, [_vp, _i, _vp, _i]),
     "pflbm_read_fields": (_i, [_vp, _vp, _i]),
@@ -163,6 +166,23 @@ def pflbm_set_graphs(d, enable: bool):
 
 def pflbm_set_tma(d, enable: bool):
     _check(load().pflbm_set_tma(d, int(bool(enable))), "pflbm_set_tma")
+
+
+STAGE_MODES = {"boxes": 0, "gather": 1}
+
+
+def pflbm_set_stage_mode(d, mode: int):
+    _check(load().pflbm_set_stage_mode(d, int(mode)), "pflbm_set_stage_mode")
+
+
+def pflbm_get_stage_mode(d) -> int:
+    return int(load().pflbm_get_stage_mode(d))
+
+
+def pflbm_autotune(d, trial_steps: int) -> int:
+    out = ctypes.c_int(-1)
+    _check(load().pflbm_autotune(d, int(trial_steps), ctypes.byref(out)), "pflbm_autotune")
+    return out.value
 
 
 def pflbm_steps_done(d) -> int:
@@ -268,6 +288,14 @@ class Domain:
     def tma(self, enable: bool = True) -> "Domain":
         pflbm_set_tma(self.h, enable)
         return self
+
+    def stage_mode(self, mode) -> "Domain":
+        pflbm_set_stage_mode(self.h, STAGE_MODES.get(mode, mode))
+        return self
+
+    def autotune(self, trial_steps: int = 20) -> str:
+        m = pflbm_autotune(self.h, trial_steps)
+        return {v: k for k, v in STAGE_MODES.items()}[m]
 
     def step(self, n: int = 1) -> "Domain":
         pflbm_step(self.h, n)

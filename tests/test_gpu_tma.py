@@ -41,7 +41,7 @@ def test_tma_tiles_match_oracle(pf, orc, form, wall):
     and the CSF normal is ill-conditioned in the 2-cell gap between drops."""
     nx, ny, phi0, p = _case(wall)
     p["form"] = form
-    d = pf.Domain(nx, ny, wall_y=wall).set_params(**p).init_phi(phi0)
+    d = pf.Domain(nx, ny, wall_y=wall).set_params(**p).stage_mode("boxes").init_phi(phi0)
     d.step(200)
     dg = d.diagnostics()
     assert dg["status"] == "PFLBM_OK", dg["status"]
@@ -63,7 +63,7 @@ def test_tma_equals_plain_staging(pf, storage, wall):
     out = []
     for tma in (True, False):
         d = pf.Domain(nx, ny, wall_y=wall, storage=storage).set_params(**p)
-        d.tma(tma)
+        d.stage_mode("boxes").tma(tma)
         d.init_phi(phi0)
         d.step(50)
         assert d.diagnostics()["status"] == "PFLBM_OK"
@@ -87,3 +87,42 @@ def test_16bit_storage_error(pf, orc, storage, tol_phi, tol_u):
     e_u = float(max(np.abs(g["ux"] - o["ux"]).max(), np.abs(g["uy"] - o["uy"]).max()))
     print(f"{storage}: max|dphi|={e_phi:.3e} max|du|={e_u:.3e} umax={np.abs(o['ux']).max():.3e}")
     assert e_phi <= tol_phi and e_u <= tol_u, (e_phi, e_u)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("wall", [False, True])
+@pytest.mark.parametrize("form", ["STF2", "CSF1"])
+def test_gather_equals_boxes(pf, storage, wall, form):
+    """Both staging modes feed the same arithmetic with the same values, so
+    the populations agree bitwise."""
+    nx, ny, phi0, p = _case(wall)
+    p["form"] = form
+    out = []
+    for mode in ("gather", "boxes"):
+        d = pf.Domain(nx, ny, wall_y=wall, storage=storage).set_params(**p).stage_mode(mode)
+        d.init_phi(phi0)
+        d.step(40)
+        out.append(d.populations())
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_autotune_leaves_state_unchanged(pf):
+    nx, ny, phi0, p = _case(True)
+    p["form"] = "PF1"
+    d = pf.Domain(nx, ny, wall_y=True).set_params(**p).init_phi(phi0)
+    d.step(7)
+    before = d.populations()
+    mode = d.autotune(5)
+    assert mode in ("boxes", "gather")
+    assert d.t == 7
+    after = d.populations()
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+    # stepping on from the tuned mode equals stepping a twin that never tuned
+    twin = pf.Domain(nx, ny, wall_y=True).set_params(**p).init_phi(phi0)
+    twin.step(7)
+    d.step(5)
+    twin.step(5)
+    for a, b in zip(d.populations(), twin.populations()):
+        np.testing.assert_array_equal(a, b)
