@@ -209,6 +209,11 @@ def run_ours(args, case):
     dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage, device=dev)
     dom.set_params(**case.params)
     dom.init_phi(case.phi0.astype(np.float32))
+    if args.stage == "auto":
+        stage = dom.autotune(10)   # untimed; leaves the state unchanged
+    else:
+        stage = args.stage
+        dom.stage_mode(stage)
     stream = dom.stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -273,6 +278,7 @@ def run_ours(args, case):
     e2e_dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage,
                            device=dev, stream=stream)
     e2e_dom.set_params(**case.params)
+    e2e_dom.stage_mode(stage)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pflbm.pflbm_init_phi(e2e_dom.h, phi_host)
@@ -297,7 +303,8 @@ def run_ours(args, case):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tr is None else tr * n_nodes,
-                "algorithmic_bytes": bpl * n_nodes, "kernel": "k_step"}
+                "algorithmic_bytes": bpl * n_nodes,
+                "kernel": "k_step_boxes" if stage == "boxes" else "k_step_gather"}
 
     if rank != 0:
         if ws > 1:
@@ -318,7 +325,8 @@ def run_ours(args, case):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "nx": case.nx, "ny": case.ny,
                    "walls": "y" if case.wall_y else "none", "form": args.form,
-                   "storage": args.storage, "l2": "flushed before every timed step",
+                   "storage": args.storage, "stage": stage,
+                   "l2": "flushed before every timed step",
                    "parallelism": f"replicas{ws}", "state_status": diag["status"]},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -341,6 +349,7 @@ def main():
     ap.add_argument("--workload", default="bubble_512x1024")
     ap.add_argument("--form", default="STF1")
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp16", "bf16"))
+    ap.add_argument("--stage", default="auto", choices=("auto", "boxes", "gather"))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
