@@ -218,6 +218,45 @@ pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device);
 
 void pflbm_destroy(pflbm_domain* d);
 
+/* ---- batch: many independent domains, one launch per time step ---------- */
+
+typedef struct pflbm_batch pflbm_batch;
+
+/* Device scratch a batch of these n domains needs: two argument records per
+ * domain and one work item per (domain, tile). */
+size_t pflbm_batch_workspace_bytes(int n, pflbm_domain* const* doms);
+
+/* Group n domains (FP32 storage, parameters and initial state set; sizes and
+ * force forms may all differ) into a batch whose steps run on cuda_stream.
+ * Each step is ONE persistent launch: CTAs walk a work-list of (domain,
+ * tile) items sorted by force form.  The domains keep their own state and
+ * remain usable one by one (diagnostics, read-back) once the batch stream
+ * has been synchronised; stepping a domain alone between batch steps is
+ * allowed.  The batch keeps the domain handles and the workspace until
+ * pflbm_batch_destroy.  Errors: EINVAL (bad domain list, 16-bit storage),
+ * ESTATE (a domain without state), ENOMEM_WS. */
+pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_workspace,
+                                size_t ws_bytes, void* cuda_stream, pflbm_batch** out);
+
+/* Advance every domain of the batch by nsteps steps (domains still at step 0
+ * first take one step of their own, which fixes d_t(phi u) = 0 there). */
+pflbm_status pflbm_batch_step(pflbm_batch* b, int nsteps);
+
+/* Replay captured CUDA graphs of batch steps (1) or launch each step (0). */
+pflbm_status pflbm_batch_set_graphs(pflbm_batch* b, int enable);
+
+/* Staging mode (PFLBM_STAGE_*) and persistent CTAs per SM of the batch
+ * kernel; pflbm_batch_autotune times trial steps of each candidate on the
+ * current states (which stay unchanged) and keeps the fastest. */
+pflbm_status pflbm_batch_set_config(pflbm_batch* b, int mode, int ctas_per_sm);
+pflbm_status pflbm_batch_autotune(pflbm_batch* b, int trial_steps, int* mode_out,
+                                  int* ctas_per_sm_out);
+
+/* Work items (domain tiles) of one batch step. */
+long long pflbm_batch_items(const pflbm_batch* b);
+
+void pflbm_batch_destroy(pflbm_batch* b);
+
 /* ---- misc ---------------------------------------------------------------- */
 
 const char* pflbm_status_str(pflbm_status s);

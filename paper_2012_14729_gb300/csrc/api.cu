@@ -696,6 +696,292 @@ void pflbm_destroy(pflbm_domain* d) {
   delete d;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batch
+// ---------------------------------------------------------------------------
+struct pflbm_batch {
+  int n;
+  pflbm_domain** doms;
+  cudaStream_t stream;
+  char* ws;
+  size_t table_off, items_off;
+  int nitems;
+  int mode, ctas_per_sm;
+  int graphs;
+  cudaGraphExec_t gexec;
+  StepArgs* host_table;  // staging of the argument table
+};
+
+namespace {
+
+constexpr int kBatchGraphSteps = 16;  // steps captured per batch graph (even)
+
+long long tiles_of(const pflbm_domain* d) {
+  return (long long)((d->nx + kTX - 1) / kTX) * ((d->ny + kTY - 1) / kTY);
+}
+
+void batch_drop_graph(pflbm_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+}
+
+// Upload the argument table from the domains' current states: entry 2 i + p
+// steps domain i from buffer cur_i ^ p; with `firsts`, domains at t = 0 get
+// the first-step flag.
+cudaError_t upload_table(pflbm_batch* b, int keep_phiu, int firsts) {
+  for (int i = 0; i < b->n; ++i) {
+    for (int p = 0; p < 2; ++p) {
+      StepArgs a = make_args(b->doms[i], b->doms[i]->cur ^ p);
+      a.first = firsts && b->doms[i]->t == 0;
+      a.macro = 0;
+      a.keep_phiu = keep_phiu;
+      b->host_table[2 * i + p] = a;
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(b->ws + b->table_off, b->host_table,
+                                  sizeof(StepArgs) * 2 * b->n, cudaMemcpyHostToDevice, b->stream);
+  // the host table is reused by the next upload: wait for this copy
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e;
+}
+
+int batch_grid(const pflbm_batch* b) {
+  const long long g = (long long)num_sms() * b->ctas_per_sm;
+  return (int)(g < b->nitems ? g : b->nitems);
+}
+
+cudaError_t batch_launch(const pflbm_batch* b, int bp) {
+  return launch_batch(b->mode, reinterpret_cast<const StepArgs*>(b->ws + b->table_off),
+                      reinterpret_cast<const int4*>(b->ws + b->items_off), b->nitems, bp,
+                      batch_grid(b), b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pflbm_batch_workspace_bytes(int n, pflbm_domain* const* doms) {
+  if (n <= 0 || !doms) return 0;
+  long long items = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!doms[i]) return 0;
+    items += tiles_of(doms[i]);
+  }
+  return align_up(sizeof(StepArgs) * 2 * (size_t)n) + align_up(sizeof(int4) * (size_t)items);
+}
+
+pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_workspace,
+                                size_t ws_bytes, void* cuda_stream, pflbm_batch** out) {
+  if (!out || n <= 0 || !doms || !dev_workspace || ((uintptr_t)dev_workspace % kAlign) != 0)
+    return PFLBM_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!doms[i] || doms[i]->storage != kFP32) {
+      set_msg("pflbm_batch_create: every domain must exist and use FP32 storage");
+      return PFLBM_EINVAL;
+    }
+    if (!doms[i]->has_state) {
+      set_msg("pflbm_batch_create: a domain has no initial state");
+      return PFLBM_ESTATE;
+    }
+  }
+  const size_t need = pflbm_batch_workspace_bytes(n, doms);
+  if (ws_bytes < need) {
+    set_msg("pflbm_batch_create: workspace too small");
+    return PFLBM_ENOMEM_WS;
+  }
+  pflbm_batch* b = new (std::nothrow) pflbm_batch;
+  if (!b) return PFLBM_EINVAL;
+  memset(b, 0, sizeof(*b));
+  b->n = n;
+  b->doms = new (std::nothrow) pflbm_domain*[n];
+  b->host_table = new (std::nothrow) StepArgs[2 * n];
+  if (!b->doms || !b->host_table) {
+    pflbm_batch_destroy(b);
+    return PFLBM_EINVAL;
+  }
+  for (int i = 0; i < n; ++i) b->doms[i] = doms[i];
+  b->stream = (cudaStream_t)cuda_stream;
+  b->ws = (char*)dev_workspace;
+  b->table_off = 0;
+  b->items_off = align_up(sizeof(StepArgs) * 2 * (size_t)n);
+  b->mode = kGather;
+  b->ctas_per_sm = batch_blocks_per_sm(kGather);
+  // work-list sorted by force form, then by domain and tile (row-major)
+  long long items = 0;
+  for (int i = 0; i < n; ++i) items += tiles_of(doms[i]);
+  int4* h = new (std::nothrow) int4[items];
+  if (!h) {
+    pflbm_batch_destroy(b);
+    return PFLBM_EINVAL;
+  }
+  long long k = 0;
+  for (int form = 0; form < 8; ++form)
+    for (int i = 0; i < n; ++i) {
+      if (doms[i]->par.force != form) continue;
+      const int ntx = (doms[i]->nx + kTX - 1) / kTX, nty = (doms[i]->ny + kTY - 1) / kTY;
+      for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) h[k++] = make_int4(i, tx * kTX, ty * kTY, form);
+    }
+  b->nitems = (int)k;
+  cudaError_t e = cudaMemcpyAsync(b->ws + b->items_off, h, sizeof(int4) * k,
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  delete[] h;
+  if (e != cudaSuccess) {
+    set_err("pflbm_batch_create", e);
+    pflbm_batch_destroy(b);
+    return PFLBM_ECUDA;
+  }
+  *out = b;
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_batch_set_graphs(pflbm_batch* b, int enable) {
+  if (!b) return PFLBM_EINVAL;
+  if (enable && b->stream == nullptr) {
+    set_msg("pflbm_batch_set_graphs: graphs need a non-default stream");
+    return PFLBM_EINVAL;
+  }
+  b->graphs = enable != 0;
+  batch_drop_graph(b);
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_batch_set_config(pflbm_batch* b, int mode, int ctas_per_sm) {
+  if (!b || mode < 0 || mode >= kNumModes || ctas_per_sm < 1 ||
+      ctas_per_sm > batch_blocks_per_sm(mode))
+    return PFLBM_EINVAL;
+  b->mode = mode;
+  b->ctas_per_sm = ctas_per_sm;
+  batch_drop_graph(b);
+  return PFLBM_OK;
+}
+
+long long pflbm_batch_items(const pflbm_batch* b) { return b ? b->nitems : -1; }
+
+pflbm_status pflbm_batch_step(pflbm_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return PFLBM_EINVAL;
+  if (nsteps == 0) return PFLBM_OK;
+  // the batch stream must see every domain's pending work
+  bool any_first = false;
+  for (int i = 0; i < b->n; ++i) {
+    pflbm_domain* d = b->doms[i];
+    any_first = any_first || d->t == 0;
+    if (d->stream != b->stream) {
+      cudaError_t e = cudaStreamSynchronize(d->stream);
+      if (e != cudaSuccess) {
+        set_err("pflbm_batch_step", e);
+        return PFLBM_ECUDA;
+      }
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  int left = nsteps, bp = 0;
+  if (any_first) {
+    // first batch step with the first-step flag of the domains at t = 0
+    e = upload_table(b, 0, 1);
+    if (e == cudaSuccess) e = batch_launch(b, 0);
+    bp = 1;
+    --left;
+  }
+  if (e == cudaSuccess) e = upload_table(b, 0, 0);
+  if (e == cudaSuccess && b->graphs && left >= kBatchGraphSteps + bp) {
+    if (bp == 1) {  // graphs start from step parity 0
+      e = batch_launch(b, 1);
+      bp = 0;
+      --left;
+    }
+    if (!b->gexec) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      for (int k = 0; k < kBatchGraphSteps && e == cudaSuccess; ++k) e = batch_launch(b, k & 1);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) b->gexec = nullptr;
+    }
+    while (e == cudaSuccess && left >= kBatchGraphSteps) {
+      e = cudaGraphLaunch(b->gexec, b->stream);
+      left -= kBatchGraphSteps;  // even: step parity unchanged
+    }
+  }
+  while (e == cudaSuccess && left > 0) {
+    e = batch_launch(b, bp);
+    bp ^= 1;
+    --left;
+  }
+  if (e != cudaSuccess) {
+    set_err("pflbm_batch_step", e);
+    return PFLBM_ECUDA;
+  }
+  for (int i = 0; i < b->n; ++i) {
+    b->doms[i]->cur ^= (nsteps & 1);
+    b->doms[i]->t += nsteps;
+    drop_graph(b->doms[i]);
+  }
+  return PFLBM_OK;
+}
+
+pflbm_status pflbm_batch_autotune(pflbm_batch* b, int trial_steps, int* mode_out,
+                                  int* ctas_per_sm_out) {
+  if (!b || trial_steps < 1) return PFLBM_EINVAL;
+  for (int i = 0; i < b->n; ++i)
+    if (b->doms[i]->t == 0) {
+      set_msg("pflbm_batch_autotune: step the batch once before tuning");
+      return PFLBM_ESTATE;
+    }
+  // trial steps write only the spare buffers and keep (phi u): state unchanged
+  cudaError_t e = upload_table(b, 1, 0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int keep_mode = b->mode, keep_cps = b->ctas_per_sm;
+  float best = 1e30f;
+  int best_mode = keep_mode, best_cps = keep_cps;
+  for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
+    for (int cps = 1; cps <= batch_blocks_per_sm(m) && e == cudaSuccess; ++cps) {
+      b->mode = m;
+      b->ctas_per_sm = cps;
+      e = batch_launch(b, 0);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = batch_launch(b, 0);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_mode = m;
+        best_cps = cps;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->mode = e == cudaSuccess ? best_mode : keep_mode;
+  b->ctas_per_sm = e == cudaSuccess ? best_cps : keep_cps;
+  batch_drop_graph(b);
+  if (e != cudaSuccess) {
+    set_err("pflbm_batch_autotune", e);
+    return PFLBM_ECUDA;
+  }
+  if (mode_out) *mode_out = best_mode;
+  if (ctas_per_sm_out) *ctas_per_sm_out = best_cps;
+  return PFLBM_OK;
+}
+
+void pflbm_batch_destroy(pflbm_batch* b) {
+  if (!b) return;
+  batch_drop_graph(b);
+  delete[] b->doms;
+  delete[] b->host_table;
+  delete b;
+}
+
 const char* pflbm_status_str(pflbm_status s) {
   switch (s) {
     case PFLBM_OK: return "ok";

@@ -1,0 +1,142 @@
+// Batched step: many independent domains of uneven sizes and force forms
+// advance together, one persistent launch per time step.  The CTAs walk a
+// work-list of (instance, tile) items sorted by force form; each item runs
+// the same per-tile passes as the single-domain kernels, with the instance's
+// arguments taken from a table in global memory (FP32 storage).
+#include "step_kernel.cuh"
+
+namespace pflbm {
+
+namespace {
+
+// shared memory of the largest form (the STF forms keep three level-1 extras)
+constexpr int kFieldsMax = Fields<kSTF1>::BYTES;
+constexpr int kArgsBytes = pad128((int)sizeof(StepArgs));
+
+template <class ST, int MODE, int NT>
+__device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, int form,
+                                         unsigned char* bx, unsigned char* fs, int x0, int y0) {
+  if constexpr (MODE == kBoxes) {
+    const BoxSrc<ST> src{bx};
+    switch (form) {
+      case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
+      case kSTF2: step_tile<kSTF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kCPF1: step_tile<kCPF1, ST, NT>(a, src, fs, x0, y0); break;
+      case kCPF2: step_tile<kCPF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kPF1: step_tile<kPF1, ST, NT>(a, src, fs, x0, y0); break;
+      case kPF2: step_tile<kPF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
+      default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
+    }
+  } else {
+    const GatherSrc<ST> src{};
+    switch (form) {
+      case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
+      case kSTF2: step_tile<kSTF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kCPF1: step_tile<kCPF1, ST, NT>(a, src, fs, x0, y0); break;
+      case kCPF2: step_tile<kCPF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kPF1: step_tile<kPF1, ST, NT>(a, src, fs, x0, y0); break;
+      case kPF2: step_tile<kPF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
+      default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
+    }
+  }
+}
+
+// table: 2 entries per instance (parity p reads buffer cur ^ p); items:
+// (instance, x0, y0, form).  The step parity `bp` selects the entries.
+template <int MODE>
+struct BatchCfg;
+template <>
+struct BatchCfg<kBoxes> {
+  static constexpr int NT = kThreadsBoxes, MINB = kBlocksBoxes;
+};
+template <>
+struct BatchCfg<kGather> {
+  // one resident CTA fewer than the single-domain gather kernel: the item
+  // loop and form dispatch need the registers (no spills at 85)
+  static constexpr int NT = kThreadsGather, MINB = kBlocksGather - 1;
+};
+
+template <class ST, int MODE>
+__global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
+    k_step_batch(const StepArgs* __restrict__ table, const int4* __restrict__ items, int nitems,
+                 int bp) {
+  constexpr int NT = BatchCfg<MODE>::NT;
+  constexpr bool kAsync = sizeof(typename ST::T) == 4;
+  extern __shared__ __align__(128) unsigned char sm[];
+  StepArgs* sa = reinterpret_cast<StepArgs*>(sm);  // this item's arguments
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kArgsBytes);
+  unsigned char* bx = sm + kArgsBytes + 128;
+  unsigned char* fs = bx + (MODE == kBoxes ? Boxes<ST>::BYTES : 0);
+
+  if constexpr (MODE == kBoxes) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+  }
+  uint32_t parity = 0u;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = items[it];
+    const StepArgs& ga = table[2 * item.x + bp];
+    // copy the instance's arguments to shared memory (16-byte words)
+    __syncthreads();  // the previous item is done with sa
+    {
+      const int4* s = reinterpret_cast<const int4*>(&ga);
+      int4* d = reinterpret_cast<int4*>(sa);
+      for (int w = threadIdx.x; w < (int)(sizeof(StepArgs) / 16); w += NT) d[w] = s[w];
+    }
+    __syncthreads();
+    const StepArgs& a = *sa;
+    const int x0 = item.y, y0 = item.z;
+    if constexpr (MODE == kBoxes) {
+      if (tma_tile<ST>(a, x0, y0)) {
+        // the tensor maps are read from the global table entry
+        if (threadIdx.x == 0) issue_tma<ST>(ga, bx, bar, x0, y0);
+        if (!wait_boxes(a, bar, parity)) return;
+        parity ^= 1u;
+      } else {
+        fill_boxes<ST, NT, kAsync>(a, bx, x0, y0);
+        if constexpr (kAsync) cp_async_wait_all();
+        __syncthreads();
+      }
+    }
+    run_item<ST, MODE, NT>(a, ga, item.w, bx, fs, x0, y0);
+  }
+}
+
+template <int MODE>
+constexpr int batch_smem() {
+  return kArgsBytes + 128 + (MODE == kBoxes ? Boxes<StoreF32>::BYTES : 0) + kFieldsMax;
+}
+
+template <int MODE>
+cudaError_t launch_batch_mode(const StepArgs* table, const int4* items, int nitems, int bp,
+                              int grid, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_batch<StoreF32, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         batch_smem<MODE>());
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_step_batch<StoreF32, MODE><<<grid, BatchCfg<MODE>::NT, batch_smem<MODE>(), s>>>(
+      table, items, nitems, bp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int batch_blocks_per_sm(int mode) {
+  return mode == kBoxes ? BatchCfg<kBoxes>::MINB : BatchCfg<kGather>::MINB;
+}
+
+cudaError_t launch_batch(int mode, const StepArgs* table, const int4* items, int nitems, int bp,
+                         int grid, cudaStream_t s) {
+  if (mode == kBoxes) return launch_batch_mode<kBoxes>(table, items, nitems, bp, grid, s);
+  return launch_batch_mode<kGather>(table, items, nitems, bp, grid, s);
+}
+
+}  // namespace pflbm

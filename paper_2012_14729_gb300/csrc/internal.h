@@ -90,6 +90,14 @@ __host__ __device__ constexpr int box_w(int elem_bytes) { return kTX + 2 * box_x
 constexpr int kBoxRowsH = kTY + 6;  // phi is needed on the tile + 3 ring
 constexpr int kBoxRowsF = kTY + 2;  // f on the tile + 1 ring
 
+// Batched step over a work-list (batch.cu): table holds 2 StepArgs per
+// instance (entry 2 i + p reads buffer cur_i ^ p), items (instance, x0, y0,
+// form); `bp` is the step parity; `grid` persistent CTAs.
+int batch_blocks_per_sm(int mode);
+int num_sms();  // streaming multiprocessors of the current device
+cudaError_t launch_batch(int mode, const StepArgs* table, const int4* items, int nitems, int bp,
+                         int grid, cudaStream_t s);
+
 cudaError_t launch_step_fp32(int form, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp16(int form, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_bf16(int form, int mode, const StepArgs& a, cudaStream_t s);

@@ -250,6 +250,7 @@ __device__ __forceinline__ bool tma_tile(const StepArgs& a, int x0, int y0) {
 }
 
 // Issue the 18 box loads of the tile at (x0, y0) into box set bx (one thread).
+// The tensor maps of `a` must live in parameter or global memory.
 template <class ST>
 __device__ __forceinline__ void issue_tma(const StepArgs& a, unsigned char* bx, uint64_t* bar,
                                           int x0, int y0) {

@@ -83,6 +83,14 @@ SIGNATURES = {
     "pflbm_save_state": (_i, [_vp, _vp, _i]),
     "pflbm_load_state": (_i, [_vp, _vp, _i]),
     "pflbm_destroy": (None, [_vp]),
+    "pflbm_batch_workspace_bytes": (_sz, [_i, ctypes.POINTER(_vp)]),
+    "pflbm_batch_create": (_i, [_i, ctypes.POINTER(_vp), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "pflbm_batch_step": (_i, [_vp, _i]),
+    "pflbm_batch_set_graphs": (_i, [_vp, _i]),
+    "pflbm_batch_set_config": (_i, [_vp, _i, _i]),
+    "pflbm_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "pflbm_batch_items": (ctypes.c_longlong, [_vp]),
+    "pflbm_batch_destroy": (None, [_vp]),
     "pflbm_status_str": (ctypes.c_char_p, [_i]),
     "pflbm_last_error": (ctypes.c_char_p, []),
     "pflbm_version": (ctypes.c_char_p, []),
@@ -232,6 +240,97 @@ def pflbm_destroy(d):
 # ---------------------------------------------------------------------------
 # convenience owner
 # ---------------------------------------------------------------------------
+
+def _handles(doms):
+    arr = (ctypes.c_void_p * len(doms))()
+    for i, d in enumerate(doms):
+        arr[i] = d.h.value if isinstance(d.h, ctypes.c_void_p) else d.h
+    return arr
+
+
+def pflbm_batch_workspace_bytes(handles) -> int:
+    return int(load().pflbm_batch_workspace_bytes(len(handles), handles))
+
+
+def pflbm_batch_create(handles, workspace_ptr, ws_bytes, stream_ptr):
+    b = ctypes.c_void_p()
+    _check(load().pflbm_batch_create(len(handles), handles, workspace_ptr, ws_bytes, stream_ptr,
+                                     ctypes.byref(b)), "pflbm_batch_create")
+    return b
+
+
+def pflbm_batch_step(b, nsteps: int):
+    _check(load().pflbm_batch_step(b, int(nsteps)), "pflbm_batch_step")
+
+
+def pflbm_batch_set_graphs(b, enable: bool):
+    _check(load().pflbm_batch_set_graphs(b, int(bool(enable))), "pflbm_batch_set_graphs")
+
+
+def pflbm_batch_set_config(b, mode: int, ctas_per_sm: int):
+    _check(load().pflbm_batch_set_config(b, int(mode), int(ctas_per_sm)), "pflbm_batch_set_config")
+
+
+def pflbm_batch_autotune(b, trial_steps: int):
+    m, c = ctypes.c_int(-1), ctypes.c_int(-1)
+    _check(load().pflbm_batch_autotune(b, int(trial_steps), ctypes.byref(m), ctypes.byref(c)),
+           "pflbm_batch_autotune")
+    return m.value, c.value
+
+
+def pflbm_batch_items(b) -> int:
+    return int(load().pflbm_batch_items(b))
+
+
+def pflbm_batch_destroy(b):
+    load().pflbm_batch_destroy(b)
+
+
+class Batch:
+    """Many Domains (FP32, initialised) advanced by one launch per step."""
+
+    def __init__(self, domains, stream=None):
+        import torch
+        self.domains = list(domains)
+        self._handles = _handles(self.domains)
+        nbytes = pflbm_batch_workspace_bytes(self._handles)
+        dev = self.domains[0].device
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        for d in self.domains:
+            d.synchronize()
+        self.h = pflbm_batch_create(self._handles, self.ws.data_ptr(), nbytes,
+                                    self.stream.cuda_stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            pflbm_batch_destroy(h)
+            self.h = None
+
+    @property
+    def items(self) -> int:
+        return pflbm_batch_items(self.h)
+
+    def step(self, n: int = 1) -> "Batch":
+        pflbm_batch_step(self.h, n)
+        return self
+
+    def graphs(self, enable: bool = True) -> "Batch":
+        pflbm_batch_set_graphs(self.h, enable)
+        return self
+
+    def config(self, mode, ctas_per_sm: int) -> "Batch":
+        pflbm_batch_set_config(self.h, STAGE_MODES.get(mode, mode), ctas_per_sm)
+        return self
+
+    def autotune(self, trial_steps: int = 5):
+        m, c = pflbm_batch_autotune(self.h, trial_steps)
+        return {v: k for k, v in STAGE_MODES.items()}[m], c
+
+    def synchronize(self):
+        self.stream.synchronize()
+
 
 def make_params(sigma=0.01, W=4.0, M=0.1, tau_h=1.0, rho1=1.0, rho2=1.0, nu1=0.1, nu2=0.1,
                 gx=0.0, gy=0.0, rho0=float("nan"), uw_bottom=0.0, uw_top=0.0, eps=1e-6,
