@@ -218,6 +218,27 @@ pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device);
 
 void pflbm_destroy(pflbm_domain* d);
 
+/* ---- adjoint: gradients of objectives of the final phi ------------------- */
+
+/* Device scratch of pflbm_adjoint_run: a checkpoint every ckpt_every steps,
+ * the pulled states of one segment, adjoint fields.  0 for invalid input
+ * (FP32 storage only). */
+size_t pflbm_adjoint_scratch_bytes(const pflbm_domain* d, int nsteps, int ckpt_every);
+
+/* Run nsteps steps from phi0 (device [ny][nx]) with the domain's parameters,
+ * checkpointing every ckpt_every steps, then run the hand-written discrete
+ * adjoint of the step (Sec. 3 scheme, every force form, periodic or walls)
+ * backwards through the steps, recomputing each segment from its checkpoint.
+ * Input dJ_dphiT: gradient of an objective J with respect to the final phi_T
+ * (device [ny][nx]).  Outputs: dJ_dphi0 (device [ny][nx]) and, on the host,
+ * dJ/dsigma and dJ/dM (FP64 accumulation; sigma through beta, kappa and the
+ * CSF-2 prefactor; M through eta).  rho0 and g are held fixed.  On return the
+ * domain holds the final state of the forward run.  Synchronises.  Errors:
+ * EINVAL, ESTATE (no parameters), ENOMEM_WS (scratch), ECUDA. */
+pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, int ckpt_every,
+                               const float* dJ_dphiT, float* dJ_dphi0, double* dJ_dsigma,
+                               double* dJ_dM, void* scratch, size_t scratch_bytes);
+
 /* ---- batch: many independent domains, one launch per time step ---------- */
 
 typedef struct pflbm_batch pflbm_batch;

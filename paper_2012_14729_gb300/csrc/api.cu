@@ -699,6 +699,149 @@ void pflbm_destroy(pflbm_domain* d) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// adjoint with checkpointing
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+  size_t ckpt, store, fields, adj[2], acc, final_state, total;
+  size_t blob;  // bytes of one state blob
+  int ncp;
+};
+
+bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
+  if (!d || nsteps < 1 || every < 1 || d->storage != kFP32) return false;
+  const size_t n = (size_t)d->nx * d->ny;
+  L->blob = align_up(pflbm_state_bytes(d));
+  L->ncp = (nsteps + every - 1) / every;
+  size_t off = 0;
+  L->ckpt = off;
+  off += (size_t)L->ncp * L->blob;
+  L->final_state = off;
+  off += L->blob;
+  L->store = off;  // per step of a segment: f [9][n], h [9][n], q [2][n]
+  off = align_up(off + (size_t)every * 20 * n * 4);
+  L->fields = off;
+  off = align_up(off + (size_t)adjoint_nfields() * n * 4);
+  for (int b = 0; b < 2; ++b) {
+    L->adj[b] = off;  // fb [9][n], hb [9][n], qb [2][n]
+    off = align_up(off + 20 * n * 4);
+  }
+  L->acc = off;
+  off = align_up(off + 4 * sizeof(double));
+  L->total = off;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pflbm_adjoint_scratch_bytes(const pflbm_domain* d, int nsteps, int ckpt_every) {
+  AdjLayout L;
+  return adj_layout(d, nsteps, ckpt_every, &L) ? L.total : 0;
+}
+
+pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, int ckpt_every,
+                               const float* dJ_dphiT, float* dJ_dphi0, double* dJ_dsigma,
+                               double* dJ_dM, void* scratch, size_t scratch_bytes) {
+  AdjLayout L;
+  if (!d || !phi0 || !dJ_dphiT || !dJ_dphi0 || !scratch ||
+      !adj_layout(d, nsteps, ckpt_every, &L)) {
+    set_msg("pflbm_adjoint_run: invalid argument (FP32 storage, nsteps, ckpt_every >= 1)");
+    return PFLBM_EINVAL;
+  }
+  if (!d->has_params) return PFLBM_ESTATE;
+  if (scratch_bytes < L.total || ((uintptr_t)scratch % kAlign) != 0) {
+    set_msg("pflbm_adjoint_run: scratch too small or misaligned");
+    return PFLBM_ENOMEM_WS;
+  }
+  char* S = (char*)scratch;
+  const size_t n = (size_t)d->nx * d->ny;
+  pflbm_status st;
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](const char* what) {
+    set_err(what, e);
+    return PFLBM_ECUDA;
+  };
+  // forward with a checkpoint every ckpt_every steps, and the final state
+  if ((st = pflbm_init_phi(d, phi0, 1)) != PFLBM_OK) return st;
+  for (int c = 0; c < L.ncp; ++c) {
+    if ((st = pflbm_save_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
+    const int seg = c + 1 < L.ncp ? ckpt_every : nsteps - c * ckpt_every;
+    if ((st = pflbm_step(d, seg)) != PFLBM_OK) return st;
+  }
+  if ((st = pflbm_save_state(d, S + L.final_state, 1)) != PFLBM_OK) return st;
+
+  // adjoint of the final state: dJ/dh_i = dJ/dphi_T for every i, f and q zero
+  int cur = 0;
+  float* adj[2] = {reinterpret_cast<float*>(S + L.adj[0]), reinterpret_cast<float*>(S + L.adj[1])};
+  double* acc = reinterpret_cast<double*>(S + L.acc);
+  e = cudaMemsetAsync(adj[0], 0, 20 * n * 4, d->stream);
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(adj[0] + (9 + i) * n, dJ_dphiT, n * 4, cudaMemcpyDeviceToDevice,
+                        d->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), d->stream);
+  if (e != cudaSuccess) return fail("adjoint setup");
+
+  float* store = reinterpret_cast<float*>(S + L.store);
+  AdjArgs A;
+  memset(&A, 0, sizeof(A));
+  A.g = AdjGeo{d->nx, d->ny, d->wall};
+  A.p = d->phys;
+  A.form = d->par.force;
+  A.F = reinterpret_cast<float*>(S + L.fields);
+  A.acc = acc;
+  for (int c = L.ncp - 1; c >= 0; --c) {
+    // recompute the segment from its checkpoint, keeping the pulled state
+    if ((st = pflbm_load_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
+    const int seg = c + 1 < L.ncp ? ckpt_every : nsteps - c * ckpt_every;
+    for (int j = 0; j < seg; ++j) {
+      float* sj = store + (size_t)j * 20 * n;
+      StepArgs a = make_args(d, d->cur);
+      e = launch_read_pops(d->storage, a, sj, sj + 9 * n, d->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sj + 18 * n, d->ws + d->lay.phiu, 2 * n * 4,
+                            cudaMemcpyDeviceToDevice, d->stream);
+      if (e != cudaSuccess) return fail("adjoint recompute");
+      if (j + 1 < seg && (st = pflbm_step(d, 1)) != PFLBM_OK) return st;
+    }
+    // reverse through the segment
+    for (int j = seg - 1; j >= 0; --j) {
+      const float* sj = store + (size_t)j * 20 * n;
+      A.fpop = sj;
+      A.hpop = sj + 9 * n;
+      A.q = sj + 18 * n;
+      A.first = (c * ckpt_every + j) == 0;
+      A.fb_in = adj[cur];
+      A.hb_in = adj[cur] + 9 * n;
+      A.qb_in = adj[cur] + 18 * n;
+      A.fb_out = adj[1 - cur];
+      A.hb_out = adj[1 - cur] + 9 * n;
+      A.qb_out = adj[1 - cur] + 18 * n;
+      if ((e = launch_adjoint_step(A, d->stream)) != cudaSuccess) return fail("adjoint step");
+      cur = 1 - cur;
+    }
+  }
+  // through the initial state to phi0
+  A.hb_in = adj[cur] + 9 * n;
+  if ((e = launch_adjoint_init(A, phi0, dJ_dphi0, d->stream)) != cudaSuccess)
+    return fail("adjoint init");
+  double h[4];
+  e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) return fail("adjoint gradients");
+  // beta4 = 3 sigma / W, kappa = 3 W sigma / 8, eta = M / (cs^2 (tau_h - 1/2))
+  const double W = d->par.W;
+  if (dJ_dsigma) *dJ_dsigma = h[0] * 3.0 / W + h[1] * 3.0 * W / 8.0 + h[3];
+  if (dJ_dM) *dJ_dM = h[2] * 3.0 / (d->par.tau_h - 0.5);
+  // leave the domain at the final state of the forward run
+  return pflbm_load_state(d, S + L.final_state, 1);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // batch
 // ---------------------------------------------------------------------------
 struct pflbm_batch {

@@ -90,6 +90,35 @@ __host__ __device__ constexpr int box_w(int elem_bytes) { return kTX + 2 * box_x
 constexpr int kBoxRowsH = kTY + 6;  // phi is needed on the tile + 3 ring
 constexpr int kBoxRowsF = kTY + 2;  // f on the tile + 1 ring
 
+// Adjoint of one step (adjoint.cu).  Populations are the pre-collision
+// (pulled) values at time t as [9][n] float32; F is adjoint_nfields() node
+// fields of scratch; acc the four FP64 parameter accumulators
+// (d/d(4 beta), d/d kappa, d/d eta, direct d/d sigma).
+struct AdjGeo {
+  int nx, ny, wall;
+};
+struct AdjArgs {
+  AdjGeo g;
+  Phys p;
+  int form, first;
+  const float* fpop;   // [9][n] f at t
+  const float* hpop;   // [9][n] h at t
+  const float* q;      // [2][n] (phi u)^{t-1}
+  const float* fb_in;  // [9][n] adjoint of f at t + 1
+  const float* hb_in;  // [9][n] adjoint of h at t + 1 (of h at 0 for the init)
+  const float* qb_in;  // [2][n] adjoint of (phi u)^t
+  float* fb_out;       // [9][n] adjoint of f at t
+  float* hb_out;       // [9][n] adjoint of h at t
+  float* qb_out;       // [2][n] adjoint of (phi u)^{t-1}
+  float* F;            // adjoint_nfields() x [n]
+  double* acc;         // [4]
+};
+int adjoint_nfields();
+cudaError_t launch_adjoint_step(const AdjArgs& A, cudaStream_t s);
+// adjoint of the initial state h = h^eq(phi0, mu0, 0): dphi0 from hb_in
+cudaError_t launch_adjoint_init(const AdjArgs& A, const float* phi0, float* dphi0,
+                                cudaStream_t s);
+
 // Batched step over a work-list (batch.cu): table holds 2 StepArgs per
 // instance (entry 2 i + p reads buffer cur_i ^ p), items (instance, x0, y0,
 // form); `bp` is the step parity; `grid` persistent CTAs.

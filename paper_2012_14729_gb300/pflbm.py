@@ -83,6 +83,9 @@ SIGNATURES = {
     "pflbm_save_state": (_i, [_vp, _vp, _i]),
     "pflbm_load_state": (_i, [_vp, _vp, _i]),
     "pflbm_destroy": (None, [_vp]),
+    "pflbm_adjoint_scratch_bytes": (_sz, [_vp, _i, _i]),
+    "pflbm_adjoint_run": (_i, [_vp, _vp, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), _vp, _sz]),
     "pflbm_batch_workspace_bytes": (_sz, [_i, ctypes.POINTER(_vp)]),
     "pflbm_batch_create": (_i, [_i, ctypes.POINTER(_vp), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     "pflbm_batch_step": (_i, [_vp, _i]),
@@ -240,6 +243,19 @@ def pflbm_destroy(d):
 # ---------------------------------------------------------------------------
 # convenience owner
 # ---------------------------------------------------------------------------
+
+def pflbm_adjoint_scratch_bytes(d, nsteps: int, ckpt_every: int) -> int:
+    return int(load().pflbm_adjoint_scratch_bytes(d, int(nsteps), int(ckpt_every)))
+
+
+def pflbm_adjoint_run(d, phi0, nsteps, ckpt_every, dJ_dphiT, dJ_dphi0, scratch):
+    """All arrays are device tensors; returns (dJ/dsigma, dJ/dM)."""
+    ds, dm = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().pflbm_adjoint_run(d, _ptr(phi0), int(nsteps), int(ckpt_every), _ptr(dJ_dphiT),
+                                    _ptr(dJ_dphi0), ctypes.byref(ds), ctypes.byref(dm),
+                                    _ptr(scratch), scratch.numel()), "pflbm_adjoint_run")
+    return ds.value, dm.value
+
 
 def _handles(doms):
     arr = (ctypes.c_void_p * len(doms))()
