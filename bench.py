@@ -54,8 +54,11 @@ def make_case(name: str, form: str):
     if name == "wave_512x1024":
         return wl.capillary_bubble("wave", form=form)
     if name == "bubble_4096x2048":
-        # same physics as the default at 8x the nodes (state 1.3 GB > L2)
+        # same physics as the default at 16x the nodes (state 1.3 GB > L2)
         return wl.capillary_bubble("bubble", form=form, nx=2048, ny=4096, R=256.0)
+    if name == "bubble_2048x1024":
+        # 4x the default's nodes, state 0.34 GB per buffer (> L2): DRAM traffic capture
+        return wl.capillary_bubble("bubble", form=form, nx=1024, ny=2048, R=128.0)
     if name == "drop_64x64":
         return wl.stationary_drop(form)
     if name == "merging_256x128":
@@ -361,11 +364,78 @@ def main():
             raise SystemExit("the batched workload has no reference arm of its own")
         run_batch(args)
         return
+    if args.workload == "adjoint_shear":
+        if args.impl == "reference":
+            raise SystemExit("the adjoint workload has no reference arm of its own")
+        run_adjoint(args)
+        return
     case = make_case(args.workload, args.form)
     if args.impl == "reference":
         run_reference(args, case)
     else:
         run_ours(args, case)
+
+
+def run_adjoint(args):
+    """Adjoint pattern on the drop-in-shear workload (512 x 256, walls at
+    -/+0.01, drop R = 40, Re = 1, Ca = 0.2, W = 4, M = 0.05, form --form):
+    `--steps` forward steps, then the full gradient run (forward with a
+    checkpoint every 200 steps, recomputation of each segment, reverse
+    sweep).  Reported: GLUPS of the forward, time of the gradient run over the
+    time of the forward, and the relative change of the gradients between
+    checkpoint intervals 200 and 50 (a consistency figure)."""
+    import torch
+    from paper_2012_14729_gb300 import build, pflbm
+
+    build.build()
+    pflbm.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    c = wl.shear_drop(args.form)
+    T, every = args.steps, min(200, args.steps)
+    stream = torch.cuda.Stream(dev)
+    d = pflbm.Domain(c.nx, c.ny, wall_y=True, stream=stream, device=dev).set_params(**c.params)
+    phi0 = torch.from_numpy(c.phi0.astype(np.float32)).to(dev)
+    target = torch.from_numpy(wl.ellipse(c.nx, c.ny, c.meta["R"], 4.0, 0.2).astype(np.float32)).to(dev)
+    d.stage_mode("gather")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # forward alone
+    d.init_phi(phi0)
+    d.step(args.warmup)
+    d.init_phi(phi0)
+    stream.synchronize()
+    e0.record(stream)
+    d.step(T)
+    e1.record(stream)
+    stream.synchronize()
+    t_fwd = e0.elapsed_time(e1)
+    phiT = d.fields(device=True)["phi"]
+    g = (2 * (phiT - target)).contiguous()
+    scratch = torch.empty(pflbm.pflbm_adjoint_scratch_bytes(d.h, T, every), dtype=torch.uint8,
+                          device=dev)
+    dphi0 = torch.empty_like(phi0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ds, dm = pflbm.pflbm_adjoint_run(d.h, phi0, T, every, g, dphi0, scratch)
+    t_adj = (time.perf_counter() - t0) * 1e3
+    every2 = max(1, every // 4)
+    scratch2 = torch.empty(pflbm.pflbm_adjoint_scratch_bytes(d.h, T, every2), dtype=torch.uint8,
+                           device=dev)
+    dphi0b = torch.empty_like(phi0)
+    ds2, dm2 = pflbm.pflbm_adjoint_run(d.h, phi0, T, every2, g, dphi0b, scratch2)
+    nodes = c.nx * c.ny
+    line = {
+        "metric": "GLUPS (coupled f+h step)", "value": nodes * T / (t_fwd * 1e-3) / 1e9,
+        "unit": "GLUPS", "n_gpus": 1, "steps": T, "warmup": args.warmup,
+        "ms_per_step": t_fwd / T, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint_shear", "nx": c.nx, "ny": c.ny, "form": args.form,
+                   "ckpt_every": every},
+        "adjoint": {"gradient_run_ms": t_adj, "forward_ms": t_fwd,
+                    "cost_over_forward": t_adj / t_fwd,
+                    "dJ_dsigma": ds, "dJ_dM": dm,
+                    "rel_change_ckpt_every_%d" % every2: max(abs(ds2 / ds - 1), abs(dm2 / dm - 1))},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_batch(args):
