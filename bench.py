@@ -76,16 +76,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(storage: str):
+def traffic_record(workload: str, storage: str, stage: str):
     """DRAM bytes per node and step of the step kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary of this workload, valid only while the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2012_14729_gb300", "csrc", "step_kernel.cuh")
     try:
         with open(path) as fh:
             rec = json.load(fh)
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        r = rec.get(storage)
+        r = rec.get(f"{workload}/{storage}/{stage}")
         if r and r.get("kernel_sha") == sha:
             return float(r["dram_bytes_per_lup"])
     except (OSError, ValueError):
@@ -302,7 +302,7 @@ def run_ours(args, case):
     bpl = BYTES_PER_LUP[args.storage]
     launch_ms = statistics.mean(per_step_ms)
     achieved = bpl * n_nodes / (launch_ms * 1e-3) / 1e9
-    tr = traffic_record(args.storage)
+    tr = traffic_record(args.workload, args.storage, stage)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tr is None else tr * n_nodes,

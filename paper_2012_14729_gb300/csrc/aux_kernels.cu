@@ -192,16 +192,20 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
   }
 }
 
+// One warp per slot: lanes take block partials in a fixed stride and the
+// warp combines them by shuffles (deterministic order).
 __global__ void k_diag_final(const double* __restrict__ partials, int nblocks,
                              double* __restrict__ out) {
-  const int j = threadIdx.x;
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j >= kNRed) return;
   double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    const double p = (j < 13) ? partials[b * kNRed + j] : 0.0;
-    v = (j == 1) ? fmax(v, p) : v + p;
-  }
-  out[j] = v;
+  if (j < 13)
+    for (int b = lane; b < nblocks; b += 32) {
+      const double p = partials[b * kNRed + j];
+      v = (j == 1) ? fmax(v, p) : v + p;
+    }
+  v = (j == 1) ? warp_max(v) : warp_sum(v);
+  if (lane == 0) out[j] = v;
 }
 
 int diag_blocks(int n_nodes, int max_blocks) {
@@ -214,7 +218,7 @@ cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, doubl
                         int max_blocks, double* red, cudaStream_t s) {
   const int nb = diag_blocks(L.nx * L.ny, max_blocks);
   k_diag_partial<<<nb, kDiagThreads, 0, s>>>(L, fields, g, partials);
-  k_diag_final<<<1, 32, 0, s>>>(partials, nb, red);
+  k_diag_final<<<1, 32 * kNRed, 0, s>>>(partials, nb, red);
   return cudaGetLastError();
 }
 
