@@ -278,6 +278,47 @@ long long pflbm_batch_items(const pflbm_batch* b);
 
 void pflbm_batch_destroy(pflbm_batch* b);
 
+/* ---- diagnostics without allocation -------------------------------------- */
+
+/* Largest lattice (nx * ny nodes) pflbm_field_diagnostics_noalloc accepts:
+ * its reduction scratch is one fixed 4 MiB device array (one 128-byte row of
+ * partial sums per 256 nodes), 4096 x 2048 nodes at most. */
+#define PFLBM_NOALLOC_MAX_NODES 8388608
+
+/* The FP64 diagnostics of pflbm_diagnostics (same sums, same pflbm_diag),
+ * computed from fields the caller already holds on the device, without
+ * allocating anything and without a domain or workspace.  The paper has no
+ * counterpart: this is a library service, not part of the method.
+ *
+ * Who needs it: code that watches a running simulation from outside it, such
+ * as a monitor thread or a host application that owns the whole device
+ * memory budget.  There cudaMalloc can fail because the lattice holds nearly
+ * all of HBM, and cudaFree waits for the whole device, so a per-call
+ * allocation would stall the simulation's own streams.  Such callers cannot
+ * lend this call a workspace either; it uses a device array compiled into
+ * the library instead and makes no cudaMalloc, cudaFree or other allocating
+ * call (its set-up included).
+ *
+ *   nx, ny  lattice size; nx * ny <= PFLBM_NOALLOC_MAX_NODES, else EINVAL
+ *           with the limit in pflbm_last_error()
+ *   fields  device memory of the current device, [PFLBM_NFIELDS][ny][nx]
+ *           float32 as pflbm_read_fields writes it (slots phi, ux, uy, P,
+ *           p_h are read); borrowed; a host pointer is rejected with EINVAL
+ *   geom    pressure-jump geometry or NULL; out: host struct, filled
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream); the
+ *           call synchronises it before returning
+ *
+ * Set-up: the first call on each device resolves the scratch array's address
+ * there (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  The array is shared by every caller in
+ * the process on that device: calls that overlap (from two host threads, or
+ * on two streams without ordering between them) race on it and may return
+ * wrong values; serialise them.  Returns EUNSTABLE if a node is non-finite
+ * (the struct is still filled), ECUDA on a CUDA error. */
+pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, const float* fields,
+                                             const pflbm_diag_geom* geom, pflbm_diag* out,
+                                             void* stream);
+
 /* ---- misc ---------------------------------------------------------------- */
 
 const char* pflbm_status_str(pflbm_status s);

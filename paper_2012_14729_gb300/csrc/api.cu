@@ -67,6 +67,8 @@ bool layout_of(int nx, int ny, int storage, Layout* L) {
 
 }  // namespace
 
+void pflbm::set_last_error(const char* msg) { set_msg(msg); }
+
 struct pflbm_domain {
   int nx, ny, wall, storage;
   cudaStream_t stream;

@@ -146,4 +146,7 @@ cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, doubl
                         int max_blocks, double* red, cudaStream_t s);
 int diag_blocks(int n_nodes, int max_blocks);
 
+// Message returned by pflbm_last_error() on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace pflbm

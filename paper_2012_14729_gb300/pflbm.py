@@ -24,6 +24,7 @@ FORMS = ("STF1", "STF2", "CPF1", "CPF2", "PF1", "PF2", "CSF1", "CSF2")
 FAMILY = {"STF": "STF1", "CPF": "CPF1", "PF": "PF1", "CSF": "CSF1"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 FIELDS = ("phi", "rho", "ux", "uy", "P", "mu", "p_h", "Fx", "Fy")
+NOALLOC_MAX_NODES = 8388608  # PFLBM_NOALLOC_MAX_NODES
 PERIODIC, WALL = 0, 1
 
 STATUS = {0: "PFLBM_OK", 1: "PFLBM_EINVAL", 2: "PFLBM_ENOMEM_WS", 3: "PFLBM_ECUDA",
@@ -94,6 +95,8 @@ SIGNATURES = {
     "pflbm_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pflbm_batch_items": (ctypes.c_longlong, [_vp]),
     "pflbm_batch_destroy": (None, [_vp]),
+    "pflbm_field_diagnostics_noalloc": (_i, [_i, _i, _vp, ctypes.POINTER(pflbm_diag_geom),
+                                         ctypes.POINTER(pflbm_diag), _vp]),
     "pflbm_status_str": (ctypes.c_char_p, [_i]),
     "pflbm_last_error": (ctypes.c_char_p, []),
     "pflbm_version": (ctypes.c_char_p, []),
@@ -221,6 +224,21 @@ def pflbm_diagnostics(d, geom: Optional[pflbm_diag_geom]):
                                   ctypes.byref(out))
     if st not in (0, 4):
         _check(st, "pflbm_diagnostics")
+    return st, out
+
+
+def pflbm_field_diagnostics_noalloc(nx: int, ny: int, fields, geom: Optional[pflbm_diag_geom],
+                                    stream=None):
+    """FP64 diagnostics of device fields [PFLBM_NFIELDS][ny][nx] through the
+    library's static scratch (no allocation); stream is a torch stream, a raw
+    handle or None (legacy default stream).  Returns (status, pflbm_diag)."""
+    out = pflbm_diag()
+    handle = getattr(stream, "cuda_stream", stream)
+    st = load().pflbm_field_diagnostics_noalloc(int(nx), int(ny), _ptr(fields),
+                                                None if geom is None else ctypes.byref(geom),
+                                                ctypes.byref(out), handle)
+    if st not in (0, 4):
+        _check(st, "pflbm_field_diagnostics_noalloc")
     return st, out
 
 

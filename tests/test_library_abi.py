@@ -82,3 +82,20 @@ def test_create_and_param_checks(lib):
 def test_status_strings(lib):
     assert lib.pflbm_status_str(0) == b"ok"
     assert b"sm_103a" in lib.pflbm_version()
+
+
+def test_noalloc_diagnostics_size_checks(lib):
+    """The no-allocation diagnostics reject sizes before any CUDA call."""
+    from paper_2012_14729_gb300 import pflbm
+    fake = 1 << 20  # never dereferenced: the size checks come first
+    out = pflbm.pflbm_diag()
+    f = lib.pflbm_field_diagnostics_noalloc
+    assert f(0, 16, fake, None, ctypes.byref(out), None) == 1
+    assert f(16, -1, fake, None, ctypes.byref(out), None) == 1
+    assert f(16, 16, fake, None, None, None) == 1
+    assert pflbm.NOALLOC_MAX_NODES == 4096 * 2048
+    assert f(4096, 2049, fake, None, ctypes.byref(out), None) == 1
+    msg = lib.pflbm_last_error().decode()
+    assert "8392704 nodes" in msg and "at most 8388608 nodes" in msg
+    hdr = open(HEADER).read()
+    assert re.search(r"#define PFLBM_NOALLOC_MAX_NODES\s+%d\b" % pflbm.NOALLOC_MAX_NODES, hdr)
