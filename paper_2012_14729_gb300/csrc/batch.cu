@@ -10,7 +10,12 @@ namespace pflbm {
 namespace {
 
 // shared memory of the largest form (the STF forms keep three level-1 extras)
-constexpr int kFieldsMax = Fields<kSTF1>::BYTES;
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int kFieldsMax =
+    cmax(cmax(cmax(Fields<kSTF1>::BYTES, Fields<kSTF2>::BYTES),
+              cmax(Fields<kCPF1>::BYTES, Fields<kCPF2>::BYTES)),
+         cmax(cmax(Fields<kPF1>::BYTES, Fields<kPF2>::BYTES),
+              cmax(Fields<kCSF1>::BYTES, Fields<kCSF2>::BYTES)));
 constexpr int kArgsBytes = pad128((int)sizeof(StepArgs));
 
 template <class ST, int MODE, int NT>

@@ -34,7 +34,7 @@ enum Form { kSTF1 = 0, kSTF2, kCPF1, kCPF2, kPF1, kPF2, kCSF1, kCSF2 };
 // Number of form-specific level-1 fields kept in shared memory.
 template <int FORM>
 __host__ __device__ constexpr int extra_fields() {
-  return (FORM == kSTF1 || FORM == kSTF2) ? 3 : ((FORM == kCSF1 || FORM == kCSF2) ? 2 : 0);
+  return (FORM == kCSF1 || FORM == kCSF2) ? 2 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -156,6 +156,23 @@ __device__ __forceinline__ Pull pull_idx(const Lattice& L, int x, int y) {
   return p;
 }
 
+// The same for a node whose 8 neighbours lie inside the domain (no wrap, no
+// ghost row): row and column offsets only.
+__device__ __forceinline__ Pull pull_idx_inner(const Lattice& L, int x, int y) {
+  const int r0 = (y + 1) * L.nx + x, rm = r0 + L.nx, rp = r0 - L.nx;
+  Pull p;
+  p.i[0] = r0;
+  p.i[1] = r0 - 1;
+  p.i[2] = rp;
+  p.i[3] = r0 + 1;
+  p.i[4] = rm;
+  p.i[5] = rp - 1;
+  p.i[6] = rp + 1;
+  p.i[7] = rm + 1;
+  p.i[8] = rm - 1;
+  return p;
+}
+
 template <class ST>
 __device__ __forceinline__ float pull_phi(const StepArgs& a, const Pull& q) {
   // summed in direction order 0..8
@@ -207,6 +224,19 @@ template <int S>
 __device__ __forceinline__ float ics_dy(const float* a, int c) {
   return (a[c + S] - a[c - S]) * (1.0f / 3.0f) +
          ((a[c + S + 1] - a[c - S + 1]) + (a[c + S - 1] - a[c - S - 1])) * (1.0f / 12.0f);
+}
+
+// The same stencils of a field given as a function of the element index
+// (products of stored fields formed at each neighbour).
+template <int S, class Fn>
+__device__ __forceinline__ float ics_dx_of(const Fn& a, int c) {
+  return (a(c + 1) - a(c - 1)) * (1.0f / 3.0f) +
+         ((a(c + S + 1) - a(c + S - 1)) + (a(c - S + 1) - a(c - S - 1))) * (1.0f / 12.0f);
+}
+template <int S, class Fn>
+__device__ __forceinline__ float ics_dy_of(const Fn& a, int c) {
+  return (a(c + S) - a(c - S)) * (1.0f / 3.0f) +
+         ((a(c + S + 1) - a(c - S + 1)) + (a(c + S - 1) - a(c - S - 1))) * (1.0f / 12.0f);
 }
 
 }  // namespace pflbm

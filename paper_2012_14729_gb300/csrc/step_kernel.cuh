@@ -103,9 +103,12 @@ struct Fields {
   static constexpr int B1X = kTX + 2, B1Y = kTY + 2;  // tile + 1 ring
   static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
   static constexpr int NE = extra_fields<FORM>();
+  // lap phi is kept past pass 2 only by the forms whose force uses it
+  static constexpr bool kLap = FORM == kPF1 || FORM == kPF2;
+  static constexpr int NS2 = 3 + (kLap ? 1 : 0) + NE;  // grad phi, mu, [lap], extras
   static constexpr int OFF_PHI = 0;
   static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
-  static constexpr int OFF_S1 = OFF_S2 + pad128((4 + NE) * N2 * 4);
+  static constexpr int OFF_S1 = OFF_S2 + pad128(NS2 * N2 * 4);
   static constexpr int BYTES = OFF_S1 + pad128(6 * N1 * 4);
 };
 
@@ -135,6 +138,7 @@ struct Boxes {
 // pulled at a node sits at box column (node column - c_ix) of its row.
 template <class ST>
 struct BoxSrc {
+  static constexpr bool kInner = false;
   using G = Boxes<ST>;
   const unsigned char* bx;
   template <int I>
@@ -211,14 +215,21 @@ struct BoxSrc {
 };
 
 // Straight from the population planes (global coordinates of the node).
-template <class ST>
+// INNER: the tile and its 3-ring pull only from inside the domain, so node
+// coordinates need no wrap or mirror and pulls no ghost row.
+template <class ST, bool INNER = false>
 struct GatherSrc {
+  static constexpr bool kInner = INNER;
+  __device__ __forceinline__ static Pull idx(const Lattice& L, int gx, int gy) {
+    if constexpr (INNER) return pull_idx_inner(L, gx, gy);
+    else return pull_idx(L, gx, gy);
+  }
   __device__ __forceinline__ float phi(const StepArgs& a, int, int, int gx, int gy) const {
-    return pull_phi<ST>(a, pull_idx(a.L, gx, gy));
+    return pull_phi<ST>(a, idx(a.L, gx, gy));
   }
   __device__ __forceinline__ void f_ring1(const StepArgs& a, int, int, int gx, int gy,
                                           float* f) const {
-    const Pull q = pull_idx(a.L, gx, gy);
+    const Pull q = idx(a.L, gx, gy);
     f[1] = load_f<ST, 1>(a, q.i[1]);
     f[2] = load_f<ST, 2>(a, q.i[2]);
     f[3] = load_f<ST, 3>(a, q.i[3]);
@@ -230,17 +241,22 @@ struct GatherSrc {
   }
   __device__ __forceinline__ void f_node(const StepArgs& a, int, int, int gx, int gy,
                                          float* f) const {
-    pull_f<ST>(a, pull_idx(a.L, gx, gy), f);
+    pull_f<ST>(a, idx(a.L, gx, gy), f);
   }
   __device__ __forceinline__ void h_node(const StepArgs& a, int, int, int gx, int gy,
                                          float* h) const {
-    pull_h<ST>(a, pull_idx(a.L, gx, gy), h);
+    pull_h<ST>(a, idx(a.L, gx, gy), h);
   }
 };
 
 // ---------------------------------------------------------------------------
 // box staging
 // ---------------------------------------------------------------------------
+// Tiles whose 3-ring and its pull sources lie inside the domain.
+__device__ __forceinline__ bool inner_tile(const Lattice& L, int x0, int y0) {
+  return x0 >= 4 && x0 + kTX + 4 <= L.nx && y0 >= 4 && y0 + kTY + 4 <= L.ny;
+}
+
 // Tiles whose 18 boxes lie inside the stored planes without wrapping.
 template <class ST>
 __device__ __forceinline__ bool tma_tile(const StepArgs& a, int x0, int y0) {
@@ -344,36 +360,45 @@ __device__ __forceinline__ bool wait_boxes(const StepArgs& a, uint64_t* bar, uin
 // ---------------------------------------------------------------------------
 // collision of an opposite pair (i, j) with c_j = -c_i, w_j = w_i:
 // f_i^+ = f_i (1 - 1/tau_f) + f_i^eq / tau_f + (1 - 1/(2 tau_f)) F_i and the
-// same for h with tau_h and H_i (Eqs. fh, P_LBM, CH_LB_force, heq_CH)
+// same for h with tau_h and H_i (Eqs. fh, P_LBM, CH_LB_force, heq_CH).
+// With s_i = 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 |u|^2, a_i = c_i.F - u.F and
+// b_i = a_i + c_i.R - u.R (R = grad rho / 3), the f update is
+//   f_i^+ = (1 - omf) f_i + w omf P + w cff a_i + s_i (w omf rho/3 + w cff b_i)
+// and the h update, with d_i = c_i.(d/dt)(phi u),
+//   h_i^+ = (1 - omh) h_i + w (omh eta mu + chh A) + (c_i.u) w omh 3 phi
+//           + d_i 3 w chh,
+// so the weight enters through per-node constants of its class (axis or
+// diagonal) and the pair shares c_i.u and d_i with opposite signs.
 // ---------------------------------------------------------------------------
 struct CollideConsts {
-  float ux, uy, Pr, rho3, uu15, Fx, Fy, uF, rx, ry, uR, omf, omf1, cff;
-  float phi3, emu, A, dtx, dty, omh, omh1, chh;
+  float ux, uy, Fx, Fy, rx, ry, uF, uR, uu15, omf1, omh1, dtx, dty;
+  float t1[2];  // w omf P
+  float t2[2];  // w omf rho / 3
+  float t3[2];  // w (1 - omf / 2)
+  float hc[2];  // w (omh eta mu + chh A)
+  float hu[2];  // 3 w omh phi
+  float hd[2];  // 3 w chh
 };
 template <int I>
 __device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, float fj, float hi,
                                              float hj, float& foi, float& foj, float& hoi,
                                              float& hoj) {
-  constexpr float w = qw(I);
+  constexpr int C = I <= 4 ? 0 : 1;
   constexpr float cx = (float)qcx(I), cy = (float)qcy(I);
   const float cu = cx * k.ux + cy * k.uy;
+  const float q = (4.5f * cu) * cu - k.uu15;
   const float l = 3.0f * cu;
-  const float q = 4.5f * cu * cu - k.uu15;
   const float si = q + l, sj = q - l;
   const float cF = cx * k.Fx + cy * k.Fy;
   const float cR = cx * k.rx + cy * k.ry;
-  const float feqi = w * (k.Pr + k.rho3 * si);
-  const float feqj = w * (k.Pr + k.rho3 * sj);
-  const float Fi = w * ((1.0f + si) * (cF - k.uF) + si * (cR - k.uR));
-  const float Fj = w * ((1.0f + sj) * (-cF - k.uF) + sj * (-cR - k.uR));
-  foi = fi * k.omf1 + feqi * k.omf + k.cff * Fi;
-  foj = fj * k.omf1 + feqj * k.omf + k.cff * Fj;
-  const float hc = k.phi3 * cu;
-  const float cdt = 3.0f * (cx * k.dtx + cy * k.dty);
-  const float heqi = w * (k.emu + hc), heqj = w * (k.emu - hc);
-  const float Hi = w * (k.A + cdt), Hj = w * (k.A - cdt);
-  hoi = hi * k.omh1 + heqi * k.omh + k.chh * Hi;
-  hoj = hj * k.omh1 + heqj * k.omh + k.chh * Hj;
+  const float ai = cF - k.uF, aj = -cF - k.uF;
+  const float bi = ai + (cR - k.uR), bj = aj - (cR + k.uR);
+  foi = fmaf(k.omf1, fi, fmaf(si, fmaf(k.t3[C], bi, k.t2[C]), fmaf(k.t3[C], ai, k.t1[C])));
+  foj = fmaf(k.omf1, fj, fmaf(sj, fmaf(k.t3[C], bj, k.t2[C]), fmaf(k.t3[C], aj, k.t1[C])));
+  const float cd = cx * k.dtx + cy * k.dty;
+  const float x = fmaf(cu, k.hu[C], cd * k.hd[C]);
+  hoi = fmaf(k.omh1, hi, k.hc[C] + x);
+  hoj = fmaf(k.omh1, hj, k.hc[C] - x);
 }
 
 // ---------------------------------------------------------------------------
@@ -388,7 +413,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   constexpr int NPT = kTX * kTY / NT;  // collision nodes per thread
   static_assert(kTX * kTY % NT == 0, "whole collision nodes per thread");
   // level-1 field slots in s2, ring-1 slots in s1
-  constexpr int GX = 0, GY = 1, LAP = 2, MU = 3, E0 = 4;
+  constexpr int GX = 0, GY = 1, MU = 2, LAP = 3, E0 = F::kLap ? 4 : 3;
   constexpr int FX = 0, FY = 1, UX = 2, UY = 3, PUX = 4, PUY = 5;
   float* sPhi = reinterpret_cast<float*>(fs + F::OFF_PHI);
   float* s2 = reinterpret_cast<float*>(fs + F::OFF_S2);
@@ -397,6 +422,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   const Phys& P = a.p;
   const int tid = threadIdx.x;
   const int nn = L.nx * L.ny;
+  constexpr bool kIn = SRC::kInner;
 
   // (phi u)^{t-1} of this thread's collision nodes, loaded first so that the
   // load latency overlaps passes 1-3
@@ -407,7 +433,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const int gx = x0 + k % kTX, gy = y0 + k / kTX;
     pu_prev_x[j] = 0.0f;
     pu_prev_y[j] = 0.0f;
-    if (!a.first && !a.macro && gx < L.nx && gy < L.ny) {
+    if (!a.first && !a.macro && (kIn || (gx < L.nx && gy < L.ny))) {
       pu_prev_x[j] = a.phiu[gy * L.nx + gx];
       pu_prev_y[j] = a.phiu[nn + gy * L.nx + gx];
     }
@@ -417,11 +443,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   for (int k = tid; k < F::N3; k += NT) {
     const int r = k / B3X, cc = k - r * B3X;
     const int yn = y0 - 3 + r;
-    if (L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
-    sPhi[k] = src.phi(a, r, cc, wrap(x0 - 3 + cc, L.nx), L.wall ? yn : wrap(yn, L.ny));
+    if (!kIn && L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
+    sPhi[k] = kIn ? src.phi(a, r, cc, x0 - 3 + cc, yn)
+                  : src.phi(a, r, cc, wrap(x0 - 3 + cc, L.nx), L.wall ? yn : wrap(yn, L.ny));
   }
   __syncthreads();
-  if (L.wall && (y0 - 3 < 0 || y0 + kTY + 3 > L.ny)) {
+  if (!kIn && L.wall && (y0 - 3 < 0 || y0 + kTY + 3 > L.ny)) {
     // mirror ghosts of phi about the wall planes
     for (int k = tid; k < F::N3; k += NT) {
       const int r = k / B3X, cc = k - r * B3X;
@@ -447,13 +474,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
                        (sPhi[c - B3X + 1] - pc) + (sPhi[c - B3X - 1] - pc)) * (1.0f / 6.0f);
     s2[GX * N2 + k] = gx;
     s2[GY * N2 + k] = gy;
-    s2[LAP * N2 + k] = lap;
+    if constexpr (F::kLap) s2[LAP * N2 + k] = lap;
     s2[MU * N2 + k] = P.beta4 * pc * ((pc - 1.0f) * (pc + 1.0f)) - P.kappa * lap;
-    if constexpr (FORM == kSTF1 || FORM == kSTF2) {
-      s2[(E0 + 0) * N2 + k] = gx * gx;
-      s2[(E0 + 1) * N2 + k] = gx * gy;
-      s2[(E0 + 2) * N2 + k] = gy * gy;
-    }
     if constexpr (FORM == kCSF1 || FORM == kCSF2) {
       const float inv = rsqrtf(gx * gx + gy * gy + P.eps2);
       s2[(E0 + 0) * N2 + k] = gx * inv;
@@ -470,15 +492,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const float gx = s2[GX * N2 + c2], gy = s2[GY * N2 + c2];
     float Fx, Fy;
     if constexpr (FORM == kSTF1 || FORM == kSTF2) {
-      const float* txx = s2 + (E0 + 0) * N2;
-      const float* txy = s2 + (E0 + 1) * N2;
-      const float* tyy = s2 + (E0 + 2) * N2;
-      Fx = -P.kappa * (ics_dx<B2X>(txx, c2) + ics_dy<B2X>(txy, c2));
-      Fy = -P.kappa * (ics_dx<B2X>(txy, c2) + ics_dy<B2X>(tyy, c2));
+      // T = grad phi (x) grad phi, formed at each neighbour from the gradient
+      const float* sgx = s2 + GX * N2;
+      const float* sgy = s2 + GY * N2;
+      const auto txx = [&](int i) { return sgx[i] * sgx[i]; };
+      const auto txy = [&](int i) { return sgx[i] * sgy[i]; };
+      const auto tyy = [&](int i) { return sgy[i] * sgy[i]; };
+      Fx = -P.kappa * (ics_dx_of<B2X>(txx, c2) + ics_dy_of<B2X>(txy, c2));
+      Fy = -P.kappa * (ics_dx_of<B2X>(txy, c2) + ics_dy_of<B2X>(tyy, c2));
       if constexpr (FORM == kSTF2) {
         // kappa grad |grad phi|^2 with |grad phi|^2 = Txx + Tyy at each node
-        Fx += P.kappa * (ics_dx<B2X>(txx, c2) + ics_dx<B2X>(tyy, c2));
-        Fy += P.kappa * (ics_dy<B2X>(txx, c2) + ics_dy<B2X>(tyy, c2));
+        Fx += P.kappa * (ics_dx_of<B2X>(txx, c2) + ics_dx_of<B2X>(tyy, c2));
+        Fy += P.kappa * (ics_dy_of<B2X>(txx, c2) + ics_dy_of<B2X>(tyy, c2));
       }
     } else if constexpr (FORM == kCPF1) {
       const float* mu = s2 + MU * N2;
@@ -508,7 +533,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     Fx += (rho - P.rho0) * P.gx;
     Fy += (rho - P.rho0) * P.gy;
     float f[9];
-    src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
+    if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, f);
+    else src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
     const float jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
     const float jy = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
     // Eq. mac: u = [sum c f + cs^2 F / 2] / (cs^2 rho)
@@ -525,7 +551,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   __syncthreads();
 
   // wall ghosts of phi u: phi (2 u_w - u) of the mirrored node
-  if (L.wall) {
+  if (!kIn && L.wall) {
     const int lb = -1 - (y0 - 1);      // ring-1 row of y = -1
     const int lt = L.ny - (y0 - 1);    // ring-1 row of y = ny
     const bool bot = lb >= 0 && lb + 1 < B1Y;
@@ -555,7 +581,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const int k = tid + j * NT;
     const int ly = k / kTX, lx = k - ly * kTX;
     const int gx = x0 + lx, gy = y0 + ly;
-    if (gx >= L.nx || gy >= L.ny) continue;
+    if (!kIn && (gx >= L.nx || gy >= L.ny)) continue;
     const int c1 = (ly + 1) * B1X + lx + 1;
     const int c2 = (ly + 2) * B2X + lx + 2;
     const float phi = sPhi[(ly + 3) * B3X + lx + 3];
@@ -614,40 +640,50 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     // relaxation: tau_f = 1/2 + mu(phi) / (cs^2 rho) (Sec. 3)
     const float mv = P.mu_mid + P.mu_dhalf * phi;
     const float omf = __fdividef(1.0f, 0.5f + 3.0f * mv * __fdividef(1.0f, rho));
+    const float cff = 1.0f - 0.5f * omf;
+    const float emu = P.eta * mu;
+    const float A = P.acoef * div;
     CollideConsts K;
     K.ux = ux;
     K.uy = uy;
-    K.Pr = Pr;
-    K.rho3 = rho * (1.0f / 3.0f);
-    K.uu15 = 1.5f * (ux * ux + uy * uy);
     K.Fx = Fx;
     K.Fy = Fy;
-    K.uF = ux * Fx + uy * Fy;
     K.rx = drx * (1.0f / 3.0f);
     K.ry = dry * (1.0f / 3.0f);
+    K.uF = ux * Fx + uy * Fy;
     K.uR = ux * K.rx + uy * K.ry;
-    K.omf = omf;
+    K.uu15 = 1.5f * (ux * ux + uy * uy);
     K.omf1 = 1.0f - omf;
-    K.cff = 1.0f - 0.5f * omf;
-    K.phi3 = 3.0f * phi;
-    K.emu = P.eta * mu;
-    K.A = P.acoef * div;
+    K.omh1 = 1.0f - P.inv_tau_h;
     K.dtx = dtx;
     K.dty = dty;
-    K.omh = P.inv_tau_h;
-    K.omh1 = 1.0f - P.inv_tau_h;
-    K.chh = P.hforce;
+    {
+      const float oP = omf * Pr, oR = omf * rho * (1.0f / 3.0f);
+      const float hb = fmaf(P.inv_tau_h, emu, P.hforce * A);
+      const float hp = 3.0f * P.inv_tau_h * phi, hd = 3.0f * P.hforce;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        constexpr float wa = qw(1), wd = qw(5);
+        const float w = c == 0 ? wa : wd;
+        K.t1[c] = w * oP;
+        K.t2[c] = w * oR;
+        K.t3[c] = w * cff;
+        K.hc[c] = w * hb;
+        K.hu[c] = w * hp;
+        K.hd[c] = w * hd;
+      }
+    }
 
     float fo[9], ho[9];
     {
       // rest population: s_0 = -1.5 |u|^2, c_0 = 0, wbar_0 = w_0 - 1
       constexpr float w0 = qw(0);
       const float s0 = -K.uu15;
-      const float feq0 = w0 * (Pr + K.rho3 * s0);
-      const float F0 = w0 * ((1.0f + s0) * (-K.uF) + s0 * (-K.uR));
-      fo[0] = f[0] * K.omf1 + feq0 * omf + K.cff * F0;
-      const float heq0 = phi + (w0 - 1.0f) * K.emu;
-      ho[0] = h[0] * K.omh1 + heq0 * K.omh + K.chh * ((w0 - 1.0f) * K.A);
+      const float a0 = -K.uF, b0 = -K.uF - K.uR;
+      fo[0] = fmaf(K.omf1, f[0],
+                   w0 * (fmaf(omf, Pr, cff * a0) + s0 * fmaf(omf, rho * (1.0f / 3.0f), cff * b0)));
+      const float heq0 = phi + (w0 - 1.0f) * emu;
+      ho[0] = fmaf(K.omh1, h[0], fmaf(P.inv_tau_h, heq0, P.hforce * ((w0 - 1.0f) * A)));
     }
     collide_pair<1>(K, f[1], f[3], h[1], h[3], fo[1], fo[3], ho[1], ho[3]);
     collide_pair<2>(K, f[2], f[4], h[2], h[4], fo[2], fo[4], ho[2], ho[4]);
@@ -665,7 +701,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     store_f<ST, 7>(a, o, fo[7]); store_h<ST, 7>(a, o, ho[7]);
     store_f<ST, 8>(a, o, fo[8]); store_h<ST, 8>(a, o, ho[8]);
 
-    if (L.wall) {
+    if (!kIn && L.wall) {
       // Ladd half-way bounce-back (Sec. 4): a population heading into the
       // wall returns to this node reversed, minus 2 w_i rho c_i.u_w (f) and
       // 2 w_i phi c_i.u_w / cs^2 (h); it is written into the ghost row the
@@ -750,7 +786,10 @@ __global__ void __launch_bounds__(kThreadsGather, kBlocksGather)
   extern __shared__ __align__(128) unsigned char sm[];
   const int ntx = (a.L.nx + kTX - 1) / kTX;
   const int x0 = (blockIdx.x % ntx) * kTX, y0 = (blockIdx.x / ntx) * kTY;
-  step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST>{}, sm, x0, y0);
+  if (inner_tile(a.L, x0, y0))
+    step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, true>{}, sm, x0, y0);
+  else
+    step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, false>{}, sm, x0, y0);
 }
 
 int num_sms();
