@@ -9,7 +9,7 @@ namespace pflbm {
 
 namespace {
 
-// shared memory of the largest form (the STF forms keep three level-1 extras)
+// shared memory of the largest form
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kFieldsMax =
     cmax(cmax(cmax(Fields<kSTF1>::BYTES, Fields<kSTF2>::BYTES),
@@ -17,6 +17,22 @@ constexpr int kFieldsMax =
          cmax(cmax(Fields<kPF1>::BYTES, Fields<kPF2>::BYTES),
               cmax(Fields<kCSF1>::BYTES, Fields<kCSF2>::BYTES)));
 constexpr int kArgsBytes = pad128((int)sizeof(StepArgs));
+
+template <class ST, int NT, bool INNER>
+__device__ __forceinline__ void gather_item(const StepArgs& a, int form, unsigned char* fs, int x0,
+                                            int y0) {
+  const GatherSrc<ST, INNER> src{};
+  switch (form) {
+    case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
+    case kSTF2: step_tile<kSTF2, ST, NT>(a, src, fs, x0, y0); break;
+    case kCPF1: step_tile<kCPF1, ST, NT>(a, src, fs, x0, y0); break;
+    case kCPF2: step_tile<kCPF2, ST, NT>(a, src, fs, x0, y0); break;
+    case kPF1: step_tile<kPF1, ST, NT>(a, src, fs, x0, y0); break;
+    case kPF2: step_tile<kPF2, ST, NT>(a, src, fs, x0, y0); break;
+    case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
+    default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
+  }
+}
 
 template <class ST, int MODE, int NT>
 __device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, int form,
@@ -33,18 +49,10 @@ __device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, 
       case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
       default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
     }
+  } else if (inner_tile(a.L, x0, y0)) {
+    gather_item<ST, NT, true>(a, form, fs, x0, y0);
   } else {
-    const GatherSrc<ST> src{};
-    switch (form) {
-      case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
-      case kSTF2: step_tile<kSTF2, ST, NT>(a, src, fs, x0, y0); break;
-      case kCPF1: step_tile<kCPF1, ST, NT>(a, src, fs, x0, y0); break;
-      case kCPF2: step_tile<kCPF2, ST, NT>(a, src, fs, x0, y0); break;
-      case kPF1: step_tile<kPF1, ST, NT>(a, src, fs, x0, y0); break;
-      case kPF2: step_tile<kPF2, ST, NT>(a, src, fs, x0, y0); break;
-      case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
-      default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
-    }
+    gather_item<ST, NT, false>(a, form, fs, x0, y0);
   }
 }
 

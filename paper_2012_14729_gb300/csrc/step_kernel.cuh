@@ -440,6 +440,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   }
 
   // ---- pass 1: phi on tile + 3 ------------------------------------------------
+#pragma unroll 2
   for (int k = tid; k < F::N3; k += NT) {
     const int r = k / B3X, cc = k - r * B3X;
     const int yn = y0 - 3 + r;
@@ -458,6 +459,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       sPhi[k] = (rm >= 0 && rm < F::B3Y) ? sPhi[rm * B3X + cc] : 0.0f;
     }
     __syncthreads();
+  }
+
+  // Float32 planes: f of this thread's first ring-1 node is loaded before
+  // pass 2 so that a gather's latency overlaps it (16-bit planes, and the
+  // STF-2 force's extra stencils, would spill the held values).  Box staging
+  // takes the same order so that both modes round identically.
+  constexpr bool kPre = sizeof(typename ST::T) == 4 && FORM != kSTF2;
+  float fpre[9];
+  if constexpr (kPre) {
+    const int ly = tid / B1X, lx = tid - ly * B1X;
+    if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, fpre);
+    else src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), fpre);
   }
 
   // ---- pass 2: grad phi, lap phi, mu, level-1 fields on tile + 2 -------------
@@ -485,7 +498,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   __syncthreads();
 
   // ---- pass 3: force, rho, u, phi u on tile + 1 -----------------------------
-  for (int k = tid; k < N1; k += NT) {
+  static_assert(N1 > NT, "every thread has a first ring-1 node");
+  auto pass3 = [&](int k, const float* f) {
     const int ly = k / B1X, lx = k - ly * B1X;
     const int c2 = (ly + 1) * B2X + lx + 1;
     const float phi = sPhi[(ly + 2) * B3X + lx + 2];
@@ -532,9 +546,6 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const float rho = P.rho_mid + P.drho_half * phi;
     Fx += (rho - P.rho0) * P.gx;
     Fy += (rho - P.rho0) * P.gy;
-    float f[9];
-    if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, f);
-    else src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
     const float jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
     const float jy = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
     // Eq. mac: u = [sum c f + cs^2 F / 2] / (cs^2 rho)
@@ -547,6 +558,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     s1[UY * N1 + k] = uy;
     s1[PUX * N1 + k] = phi * ux;
     s1[PUY * N1 + k] = phi * uy;
+  };
+  auto load_ring1 = [&](int k, float* f) {
+    const int ly = k / B1X, lx = k - ly * B1X;
+    if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, f);
+    else src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
+  };
+  if constexpr (kPre) pass3(tid, fpre);
+  for (int k = kPre ? tid + NT : tid; k < N1; k += NT) {
+    float f[9];
+    load_ring1(k, f);
+    pass3(k, f);
   }
   __syncthreads();
 

@@ -93,8 +93,11 @@ def test_16bit_storage_error(pf, orc, storage, tol_phi, tol_u):
 @pytest.mark.parametrize("wall", [False, True])
 @pytest.mark.parametrize("form", ["STF2", "CSF1"])
 def test_gather_equals_boxes(pf, storage, wall, form):
-    """Both staging modes feed the same arithmetic with the same values, so
-    the populations agree bitwise."""
+    """Both staging modes feed the same arithmetic with the same values; the
+    two kernels are compiled separately and may contract multiply-adds
+    differently, so the populations agree to float32 rounding (one unit in
+    the last place of the 16-bit code where a rounding difference lands on a
+    coding boundary)."""
     nx, ny, phi0, p = _case(wall)
     p["form"] = form
     out = []
@@ -103,8 +106,15 @@ def test_gather_equals_boxes(pf, storage, wall, form):
         d.init_phi(phi0)
         d.step(40)
         out.append(d.populations())
+    # f are small deviations formed from O(1) terms (rho/3, P): their
+    # rounding, grown over 40 steps, is ~1e-10 absolute, not relative to
+    # |f| (~3e-5 here); a staging error would differ by O(|f|) and O(|h|)
+    rel = 1e-6 if storage == "fp32" else 2e-3
     for a, b in zip(out[0], out[1]):
-        np.testing.assert_array_equal(a, b)
+        for i in range(9):
+            scale = float(np.abs(b[i]).max())
+            err = float(np.abs(a[i] - b[i]).max())
+            assert err <= rel * scale + 1e-8, (i, scale, err)
 
 
 def test_autotune_leaves_state_unchanged(pf):
@@ -119,9 +129,12 @@ def test_autotune_leaves_state_unchanged(pf):
     after = d.populations()
     for a, b in zip(before, after):
         np.testing.assert_array_equal(a, b)
-    # stepping on from the tuned mode equals stepping a twin that never tuned
+    # stepping on from the tuned mode equals stepping a twin that never tuned,
+    # switched to the same mode after the same first steps (the two modes
+    # agree only to rounding)
     twin = pf.Domain(nx, ny, wall_y=True).set_params(**p).init_phi(phi0)
     twin.step(7)
+    twin.stage_mode(mode)
     d.step(5)
     twin.step(5)
     for a, b in zip(d.populations(), twin.populations()):
