@@ -415,6 +415,7 @@ def run_adjoint(args):
     phi0 = torch.from_numpy(c.phi0.astype(np.float32)).to(dev)
     target = torch.from_numpy(wl.ellipse(c.nx, c.ny, c.meta["R"], 4.0, 0.2).astype(np.float32)).to(dev)
     d.stage_mode("gather")
+    d.graphs(True)  # the forward, alone and inside the gradient run, replays graphs
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # forward alone
     d.init_phi(phi0)

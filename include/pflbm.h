@@ -220,15 +220,22 @@ void pflbm_destroy(pflbm_domain* d);
 
 /* ---- adjoint: gradients of objectives of the final phi ------------------- */
 
-/* Device scratch of pflbm_adjoint_run: a checkpoint every ckpt_every steps,
- * the pulled states of one segment, adjoint fields.  0 for invalid input
- * (FP32 storage only). */
+/* Device scratch of pflbm_adjoint_run: a checkpoint at the start of every
+ * segment of ckpt_every steps but the last, the tape of one segment (24
+ * float32 planes of nx * ny per step: pulled f, phi, grad phi, lap phi, mu,
+ * force values, u, P, div(phi u), d_t(phi u)), two adjoint states and work
+ * planes.  0 for invalid input (FP32 storage only). */
 size_t pflbm_adjoint_scratch_bytes(const pflbm_domain* d, int nsteps, int ckpt_every);
 
 /* Run nsteps steps from phi0 (device [ny][nx]) with the domain's parameters,
  * checkpointing every ckpt_every steps, then run the hand-written discrete
  * adjoint of the step (Sec. 3 scheme, every force form, periodic or walls)
- * backwards through the steps, recomputing each segment from its checkpoint.
+ * backwards through the steps.  Each segment but the last is recomputed from
+ * its checkpoint by a taping step that records the step's intermediates; the
+ * last is taped during the forward run (ckpt_every >= nsteps: no
+ * recomputation at all).  Recomputation and reverse sweep of a segment are
+ * replayed from CUDA graphs when the domain's stream can be captured (not on
+ * the legacy default stream); the first call on a stream captures them.
  * Input dJ_dphiT: gradient of an objective J with respect to the final phi_T
  * (device [ny][nx]).  Outputs: dJ_dphi0 (device [ny][nx]) and, on the host,
  * dJ/dsigma and dJ/dM (FP64 accumulation; sigma through beta, kappa and the

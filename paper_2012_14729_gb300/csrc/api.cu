@@ -706,8 +706,9 @@ void pflbm_destroy(pflbm_domain* d) {
 namespace {
 
 struct AdjLayout {
-  size_t ckpt, store, fields, adj[2], acc, final_state, total;
-  size_t blob;  // bytes of one state blob
+  size_t ckpt, tape, work, adj[2], acc, final_state, total;
+  size_t blob;       // bytes of one state blob
+  size_t tape_step;  // bytes of one step's tape
   int ncp;
 };
 
@@ -717,22 +718,64 @@ bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
   L->blob = align_up(pflbm_state_bytes(d));
   L->ncp = (nsteps + every - 1) / every;
   size_t off = 0;
-  L->ckpt = off;
-  off += (size_t)L->ncp * L->blob;
+  L->ckpt = off;  // the start of every segment but the last (taped in the forward run)
+  off += (size_t)(L->ncp - 1) * L->blob;
   L->final_state = off;
   off += L->blob;
-  L->store = off;  // per step of a segment: f [9][n], h [9][n], q [2][n]
-  off = align_up(off + (size_t)every * 20 * n * 4);
-  L->fields = off;
-  off = align_up(off + (size_t)adjoint_nfields() * n * 4);
+  L->tape_step = align_up((size_t)kTapePlanes * n * 4);
+  L->tape = off;  // one tape per step of a segment
+  off += (size_t)(every < nsteps ? every : nsteps) * L->tape_step;
+  L->work = off;
+  off = align_up(off + (size_t)kWorkPlanes * n * 4);
   for (int b = 0; b < 2; ++b) {
-    L->adj[b] = off;  // fb [9][n], hb [9][n], qb [2][n]
-    off = align_up(off + 20 * n * 4);
+    L->adj[b] = off;
+    off = align_up(off + (size_t)kAdjPlanes * n * 4);
   }
   L->acc = off;
   off = align_up(off + 4 * sizeof(double));
   L->total = off;
   return true;
+}
+
+// Graphs of one adjoint run: the recomputation of a segment keyed by (first
+// segment, full length) and its reverse sweep keyed by (first segment, parity
+// of the adjoint buffers, full length).
+struct AdjGraphs {
+  cudaGraphExec_t rec[2][2] = {};
+  cudaGraphExec_t rev[2][2][2] = {};
+  ~AdjGraphs() {
+    for (auto& a : rec)
+      for (auto& g : a)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto& a : rev)
+      for (auto& b : a)
+        for (auto& g : b)
+          if (g) cudaGraphExecDestroy(g);
+  }
+};
+
+// Run a sequence of launches on stream s from the graph in *cache, capturing
+// and instantiating it on first use; on a stream that cannot be captured (the
+// legacy default stream) the launches run directly.
+template <class Fn>
+cudaError_t run_captured(cudaStream_t s, cudaGraphExec_t* cache, Fn&& launches) {
+  if (*cache) return cudaGraphLaunch(*cache, s);
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return launches();
+  }
+  const cudaError_t el = launches();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  if (el != cudaSuccess) e = el;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(cache, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *cache = nullptr;
+    return e;
+  }
+  return cudaGraphLaunch(*cache, s);
 }
 
 }  // namespace
@@ -766,67 +809,88 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
     set_err(what, e);
     return PFLBM_ECUDA;
   };
-  // forward with a checkpoint every ckpt_every steps, and the final state
+  // forward with a checkpoint every ckpt_every steps and the final state; the
+  // last segment is taped on the way, so its reverse needs no recomputation
+  if ((e = setup_tape_step(d->par.force)) != cudaSuccess) return fail("adjoint set-up");
   if ((st = pflbm_init_phi(d, phi0, 1)) != PFLBM_OK) return st;
   for (int c = 0; c < L.ncp; ++c) {
-    if ((st = pflbm_save_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
     const int seg = c + 1 < L.ncp ? ckpt_every : nsteps - c * ckpt_every;
-    if ((st = pflbm_step(d, seg)) != PFLBM_OK) return st;
+    if (c + 1 < L.ncp) {
+      if ((st = pflbm_save_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
+      if ((st = pflbm_step(d, seg)) != PFLBM_OK) return st;
+      continue;
+    }
+    for (int j = 0; j < seg; ++j) {
+      StepArgs a = make_args(d, d->cur);
+      a.first = d->t == 0;
+      a.tape = reinterpret_cast<float*>(S + L.tape + (size_t)j * L.tape_step);
+      if ((e = launch_tape_step(d->par.force, a, d->stream)) != cudaSuccess)
+        return fail("adjoint forward");
+      d->cur = 1 - d->cur;
+      d->t += 1;
+    }
   }
   if ((st = pflbm_save_state(d, S + L.final_state, 1)) != PFLBM_OK) return st;
 
-  // adjoint of the final state: dJ/dh_i = dJ/dphi_T for every i, f and q zero
+  // adjoint of the final state: dJ/dh_i = dJ/dphi_T for every i (the per-node
+  // scalar of h), f and q zero
   int cur = 0;
   float* adj[2] = {reinterpret_cast<float*>(S + L.adj[0]), reinterpret_cast<float*>(S + L.adj[1])};
   double* acc = reinterpret_cast<double*>(S + L.acc);
-  e = cudaMemsetAsync(adj[0], 0, 20 * n * 4, d->stream);
-  for (int i = 0; i < 9 && e == cudaSuccess; ++i)
-    e = cudaMemcpyAsync(adj[0] + (9 + i) * n, dJ_dphiT, n * 4, cudaMemcpyDeviceToDevice,
+  e = cudaMemsetAsync(adj[0], 0, (size_t)kAdjPlanes * n * 4, d->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(adj[0] + (size_t)AP_PHI * n, dJ_dphiT, n * 4, cudaMemcpyDeviceToDevice,
                         d->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), d->stream);
   if (e != cudaSuccess) return fail("adjoint setup");
 
-  float* store = reinterpret_cast<float*>(S + L.store);
   AdjArgs A;
   memset(&A, 0, sizeof(A));
   A.g = AdjGeo{d->nx, d->ny, d->wall};
   A.p = d->phys;
   A.form = d->par.force;
-  A.F = reinterpret_cast<float*>(S + L.fields);
+  A.W = reinterpret_cast<float*>(S + L.work);
   A.acc = acc;
+  AdjGraphs graphs;
   for (int c = L.ncp - 1; c >= 0; --c) {
-    // recompute the segment from its checkpoint, keeping the pulled state
-    if ((st = pflbm_load_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
     const int seg = c + 1 < L.ncp ? ckpt_every : nsteps - c * ckpt_every;
-    for (int j = 0; j < seg; ++j) {
-      float* sj = store + (size_t)j * 20 * n;
-      StepArgs a = make_args(d, d->cur);
-      e = launch_read_pops(d->storage, a, sj, sj + 9 * n, d->stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sj + 18 * n, d->ws + d->lay.phiu, 2 * n * 4,
-                            cudaMemcpyDeviceToDevice, d->stream);
+    const int first = c == 0, full = seg == ckpt_every;
+    // recompute the segment from its checkpoint (loaded into buffer 0),
+    // taping every step (the last segment was taped by the forward run)
+    if (c + 1 < L.ncp) {
+      if ((st = pflbm_load_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
+      e = run_captured(d->stream, &graphs.rec[first][full], [&]() -> cudaError_t {
+        for (int j = 0; j < seg; ++j) {
+          StepArgs a = make_args(d, j & 1);
+          a.first = first && j == 0;
+          a.tape = reinterpret_cast<float*>(S + L.tape + (size_t)j * L.tape_step);
+          const cudaError_t el = launch_tape_step(d->par.force, a, d->stream);
+          if (el != cudaSuccess) return el;
+        }
+        return cudaSuccess;
+      });
       if (e != cudaSuccess) return fail("adjoint recompute");
-      if (j + 1 < seg && (st = pflbm_step(d, 1)) != PFLBM_OK) return st;
     }
     // reverse through the segment
-    for (int j = seg - 1; j >= 0; --j) {
-      const float* sj = store + (size_t)j * 20 * n;
-      A.fpop = sj;
-      A.hpop = sj + 9 * n;
-      A.q = sj + 18 * n;
-      A.first = (c * ckpt_every + j) == 0;
-      A.fb_in = adj[cur];
-      A.hb_in = adj[cur] + 9 * n;
-      A.qb_in = adj[cur] + 18 * n;
-      A.fb_out = adj[1 - cur];
-      A.hb_out = adj[1 - cur] + 9 * n;
-      A.qb_out = adj[1 - cur] + 18 * n;
-      if ((e = launch_adjoint_step(A, d->stream)) != cudaSuccess) return fail("adjoint step");
-      cur = 1 - cur;
-    }
+    const int cur0 = cur;
+    e = run_captured(d->stream, &graphs.rev[first][cur0][full], [&]() -> cudaError_t {
+      int cc = cur0;
+      for (int j = seg - 1; j >= 0; --j) {
+        A.tape = reinterpret_cast<const float*>(S + L.tape + (size_t)j * L.tape_step);
+        A.first = first && j == 0;
+        A.ain = adj[cc];
+        A.aout = adj[1 - cc];
+        const cudaError_t el = launch_adjoint_step(A, d->stream);
+        if (el != cudaSuccess) return el;
+        cc = 1 - cc;
+      }
+      return cudaSuccess;
+    });
+    if (e != cudaSuccess) return fail("adjoint step");
+    cur = (seg & 1) ? 1 - cur0 : cur0;
   }
   // through the initial state to phi0
-  A.hb_in = adj[cur] + 9 * n;
+  A.ain = adj[cur];
   if ((e = launch_adjoint_init(A, phi0, dJ_dphi0, d->stream)) != cudaSuccess)
     return fail("adjoint init");
   double h[4];

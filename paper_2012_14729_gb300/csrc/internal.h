@@ -64,6 +64,16 @@ struct StepArgs {
   int first;          // first step of a run: d_t(phi u) = 0
   int macro;          // 1: write fields instead of colliding
   int keep_phiu;      // 1: do not write (phi u)^t back (autotuning trial steps)
+  float* tape;        // taping step only: [kTapePlanes][ny][nx] of this step
+};
+
+// Planes the taping step records per node for the adjoint: the pulled f, then
+// phi, grad phi, lap phi, mu, the force-form values A0/A1 (STF: F_sf; CPF-1:
+// grad mu; PF-2: grad lap phi; CSF: div n), the total force, u, P, div(phi u)
+// and d_t(phi u).
+enum TapePlane {
+  TP_F0 = 0, TP_PHI = 9, TP_GX, TP_GY, TP_L, TP_MU, TP_A0, TP_A1, TP_FX, TP_FY, TP_UX, TP_UY,
+  TP_PR, TP_DIV, TP_DTX, TP_DTY, kTapePlanes
 };
 
 // Tile of the fused step kernel.
@@ -90,10 +100,17 @@ __host__ __device__ constexpr int box_w(int elem_bytes) { return kTX + 2 * box_x
 constexpr int kBoxRowsH = kTY + 6;  // phi is needed on the tile + 3 ring
 constexpr int kBoxRowsF = kTY + 2;  // f on the tile + 1 ring
 
-// Adjoint of one step (adjoint.cu).  Populations are the pre-collision
-// (pulled) values at time t as [9][n] float32; F is adjoint_nfields() node
-// fields of scratch; acc the four FP64 parameter accumulators
-// (d/d(4 beta), d/d kappa, d/d eta, direct d/d sigma).
+// Adjoint of one step (adjoint.cu), float32 planes of n = nx ny nodes.
+// Adjoint state between reverse steps: the adjoint of the pre-collision
+// populations is kept as per-population parts plus per-node scalars added to
+// every population when it is read (f_i: AP_F0 + i + AP_SB + c_i . AP_J;
+// h_i: AP_H0 + i + AP_PHI), and the adjoint of (phi u)^{t-1}.
+enum AdjPlane { AP_F0 = 0, AP_H0 = 9, AP_SB = 18, AP_JX, AP_JY, AP_PHI, AP_QX, AP_QY, kAdjPlanes };
+// Work planes of one reverse step.
+enum WorkPlane {
+  B_PHI, B_RHO, B_UX, B_UY, B_P, B_FX, B_FY, B_GX, B_GY, B_MU, B_DIV, B_DTX, B_DTY, B_L, B_W0,
+  B_W1, B_W2, kWorkPlanes
+};
 struct AdjGeo {
   int nx, ny, wall;
 };
@@ -101,21 +118,19 @@ struct AdjArgs {
   AdjGeo g;
   Phys p;
   int form, first;
-  const float* fpop;   // [9][n] f at t
-  const float* hpop;   // [9][n] h at t
-  const float* q;      // [2][n] (phi u)^{t-1}
-  const float* fb_in;  // [9][n] adjoint of f at t + 1
-  const float* hb_in;  // [9][n] adjoint of h at t + 1 (of h at 0 for the init)
-  const float* qb_in;  // [2][n] adjoint of (phi u)^t
-  float* fb_out;       // [9][n] adjoint of f at t
-  float* hb_out;       // [9][n] adjoint of h at t
-  float* qb_out;       // [2][n] adjoint of (phi u)^{t-1}
-  float* F;            // adjoint_nfields() x [n]
-  double* acc;         // [4]
+  const float* tape;  // [kTapePlanes][n] recorded by the taping step at t
+  const float* ain;   // [kAdjPlanes][n] adjoint state at t + 1
+  float* aout;        // [kAdjPlanes][n] adjoint state at t
+  float* W;           // [kWorkPlanes][n]
+  double* acc;        // [4]: d/d(4 beta), d/d kappa, d/d eta, direct d/d sigma
 };
-int adjoint_nfields();
+// Taping step (the plain step plus the record of its intermediates in a.tape);
+// setup_tape_step sets its kernel attributes and must precede a capture.
+cudaError_t setup_tape_step(int form);
+cudaError_t launch_tape_step(int form, const StepArgs& a, cudaStream_t s);
+// Reverse of one step: 4 kernels.
 cudaError_t launch_adjoint_step(const AdjArgs& A, cudaStream_t s);
-// adjoint of the initial state h = h^eq(phi0, mu0, 0): dphi0 from hb_in
+// Adjoint of the initial state h = h^eq(phi0, mu0, 0): dphi0 from A.ain.
 cudaError_t launch_adjoint_init(const AdjArgs& A, const float* phi0, float* dphi0,
                                 cudaStream_t s);
 

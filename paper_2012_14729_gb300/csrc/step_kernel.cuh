@@ -96,15 +96,16 @@ __host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; 
 // ---------------------------------------------------------------------------
 // shared-memory geometry: per-tile fields, and the box set of kBoxes
 // ---------------------------------------------------------------------------
-template <int FORM>
+template <int FORM, bool TAPE = false>
 struct Fields {
   static constexpr int B3X = kTX + 6, B3Y = kTY + 6;  // tile + 3 ring
   static constexpr int B2X = kTX + 4, B2Y = kTY + 4;  // tile + 2 ring
   static constexpr int B1X = kTX + 2, B1Y = kTY + 2;  // tile + 1 ring
   static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
   static constexpr int NE = extra_fields<FORM>();
-  // lap phi is kept past pass 2 only by the forms whose force uses it
-  static constexpr bool kLap = FORM == kPF1 || FORM == kPF2;
+  // lap phi is kept past pass 2 only by the forms whose force uses it (and
+  // by the taping step, which records it)
+  static constexpr bool kLap = FORM == kPF1 || FORM == kPF2 || TAPE;
   static constexpr int NS2 = 3 + (kLap ? 1 : 0) + NE;  // grad phi, mu, [lap], extras
   static constexpr int OFF_PHI = 0;
   static constexpr int OFF_S2 = OFF_PHI + pad128(N3 * 4);
@@ -404,10 +405,12 @@ __device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, f
 // ---------------------------------------------------------------------------
 // one tile: passes 1-4, populations from SRC, fields in shared memory fs
 // ---------------------------------------------------------------------------
-template <int FORM, class ST, int NT, class SRC>
+// TAPE: also record, per interior node, the step's intermediates that the
+// adjoint reads (plane layout of the TapePlane enum, a.tape + plane * nx ny).
+template <int FORM, class ST, int NT, class SRC, bool TAPE = false>
 __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, unsigned char* fs,
                                           int x0, int y0) {
-  using F = Fields<FORM>;
+  using F = Fields<FORM, TAPE>;
   constexpr int B3X = F::B3X, B2X = F::B2X, B1X = F::B1X, B1Y = F::B1Y;
   constexpr int N2 = F::N2, N1 = F::N1;
   constexpr int NPT = kTX * kTY / NT;  // collision nodes per thread
@@ -505,6 +508,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const float phi = sPhi[(ly + 2) * B3X + lx + 2];
     const float gx = s2[GX * N2 + c2], gy = s2[GY * N2 + c2];
     float Fx, Fy;
+    float a0 = 0.0f, a1 = 0.0f;  // what the force's adjoint needs (TapePlane TP_A0/1)
     if constexpr (FORM == kSTF1 || FORM == kSTF2) {
       // T = grad phi (x) grad phi, formed at each neighbour from the gradient
       const float* sgx = s2 + GX * N2;
@@ -519,10 +523,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
         Fx += P.kappa * (ics_dx_of<B2X>(txx, c2) + ics_dx_of<B2X>(tyy, c2));
         Fy += P.kappa * (ics_dy_of<B2X>(txx, c2) + ics_dy_of<B2X>(tyy, c2));
       }
+      a0 = Fx;
+      a1 = Fy;
     } else if constexpr (FORM == kCPF1) {
       const float* mu = s2 + MU * N2;
-      Fx = -phi * ics_dx<B2X>(mu, c2);
-      Fy = -phi * ics_dy<B2X>(mu, c2);
+      a0 = ics_dx<B2X>(mu, c2);
+      a1 = ics_dy<B2X>(mu, c2);
+      Fx = -phi * a0;
+      Fy = -phi * a1;
     } else if constexpr (FORM == kCPF2) {
       const float mu = s2[MU * N2 + c2];
       Fx = mu * gx;
@@ -533,10 +541,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       Fy = -P.kappa * gy * lap;
     } else if constexpr (FORM == kPF2) {
       const float* lap = s2 + LAP * N2;
-      Fx = P.kappa * phi * ics_dx<B2X>(lap, c2);
-      Fy = P.kappa * phi * ics_dy<B2X>(lap, c2);
+      a0 = ics_dx<B2X>(lap, c2);
+      a1 = ics_dy<B2X>(lap, c2);
+      Fx = P.kappa * phi * a0;
+      Fy = P.kappa * phi * a1;
     } else {  // CSF-1, CSF-2
       const float divn = ics_dx<B2X>(s2 + E0 * N2, c2) + ics_dy<B2X>(s2 + (E0 + 1) * N2, c2);
+      a0 = divn;
       float coef;
       if constexpr (FORM == kCSF1) coef = -P.kappa * sqrtf(gx * gx + gy * gy) * divn;
       else coef = -P.half_sigma * divn;
@@ -558,6 +569,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     s1[UY * N1 + k] = uy;
     s1[PUX * N1 + k] = phi * ux;
     s1[PUY * N1 + k] = phi * uy;
+    if constexpr (TAPE) {
+      const int gxn = x0 - 1 + lx, gyn = y0 - 1 + ly;
+      if (lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY && gxn < L.nx && gyn < L.ny) {
+        float* t = a.tape + gyn * L.nx + gxn;
+        t[TP_A0 * nn] = a0;
+        t[TP_A1 * nn] = a1;
+        t[TP_FX * nn] = Fx;
+        t[TP_FY * nn] = Fy;
+        t[TP_UX * nn] = ux;
+        t[TP_UY * nn] = uy;
+      }
+    }
   };
   auto load_ring1 = [&](int k, float* f) {
     const int ly = k / B1X, lx = k - ly * B1X;
@@ -654,6 +677,21 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     if (!a.keep_phiu) {
       a.phiu[n_idx] = pux;
       a.phiu[nn + n_idx] = puy;
+    }
+
+    if constexpr (TAPE) {
+      float* t = a.tape + n_idx;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) t[(TP_F0 + i) * nn] = f[i];
+      t[TP_PHI * nn] = phi;
+      t[TP_GX * nn] = Gx;
+      t[TP_GY * nn] = Gy;
+      t[TP_L * nn] = s2[LAP * N2 + c2];
+      t[TP_MU * nn] = mu;
+      t[TP_PR * nn] = Pr;
+      t[TP_DIV * nn] = div;
+      t[TP_DTX * nn] = dtx;
+      t[TP_DTY * nn] = dty;
     }
 
     float h[9];
@@ -812,6 +850,22 @@ __global__ void __launch_bounds__(kThreadsGather, kBlocksGather)
     step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, true>{}, sm, x0, y0);
   else
     step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, false>{}, sm, x0, y0);
+}
+
+// Taping step of the adjoint's recomputation (float32 storage, gathers): the
+// plain step plus the record of its intermediates in a.tape.  Built for three
+// CTAs per SM so that the extra live values do not spill.
+template <int FORM>
+__global__ void __launch_bounds__(kThreadsGather, 3) k_step_tape(const __grid_constant__ StepArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int ntx = (a.L.nx + kTX - 1) / kTX;
+  const int x0 = (blockIdx.x % ntx) * kTX, y0 = (blockIdx.x / ntx) * kTY;
+  if (inner_tile(a.L, x0, y0))
+    step_tile<FORM, StoreF32, kThreadsGather, GatherSrc<StoreF32, true>, true>(
+        a, GatherSrc<StoreF32, true>{}, sm, x0, y0);
+  else
+    step_tile<FORM, StoreF32, kThreadsGather, GatherSrc<StoreF32, false>, true>(
+        a, GatherSrc<StoreF32, false>{}, sm, x0, y0);
 }
 
 int num_sms();

@@ -144,3 +144,27 @@ def test_domain_left_at_final_state(pf):
     assert d.t == T
     for a, b in zip(d.populations(), ref.populations()):
         np.testing.assert_array_equal(a, b)
+
+
+def test_legacy_stream_runs_without_graphs(pf):
+    """On the legacy default stream (which cannot be captured) the segments
+    run as plain launches: the gradients equal those of a graph replay."""
+    import torch
+    nx, ny, phi0, target, p = _case(True, "STF2")
+    T, every = 10, 4
+    out = []
+    for stream in (None, torch.cuda.default_stream()):
+        d = pf.Domain(nx, ny, wall_y=True, stream=stream).set_params(**p)
+        dev = torch.device("cuda")
+        phi0_t = torch.from_numpy(phi0).to(dev)
+        g = torch.from_numpy(target).to(dev)
+        scratch = torch.empty(pf.pflbm_adjoint_scratch_bytes(d.h, T, every), dtype=torch.uint8,
+                              device=dev)
+        dphi0 = torch.empty_like(phi0_t)
+        torch.cuda.synchronize()
+        ds, dm = pf.pflbm_adjoint_run(d.h, phi0_t, T, every, g, dphi0, scratch)
+        out.append((ds, dm, dphi0.cpu().numpy()))
+    # parameter gradients are FP64 atomic sums (order may vary): 1e-12
+    assert abs(out[0][0] - out[1][0]) <= 1e-12 * abs(out[0][0])
+    assert abs(out[0][1] - out[1][1]) <= 1e-12 * abs(out[0][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
