@@ -167,6 +167,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The job's value of a per-rank time: its maximum over the ranks (an
+    all-reduce on the initialised process group; the value itself on one)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_glups(ws: int, n_nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of ws independent replicas of n_nodes nodes that
+    each advanced `steps` steps in `seconds` (the slowest rank's time)."""
+    return ws * n_nodes * steps / seconds / 1e9
+
+
 def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2):
     """Oracle steps on the full grid of the workload until `seconds` of CPU
     work: returns (GLUPS, steps, threads)."""
@@ -278,14 +296,9 @@ def run_ours(args, case):
     time.sleep(0.15)  # one more clock sample after the timed region
     clk.__exit__(None, None, None)
     per_step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    t_ms = sum(per_step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(sum(per_step_ms), ws, dev)
     ms_per_step = t_ms / args.steps
-    value = ws * n_nodes * args.steps / (t_ms * 1e-3) / 1e9
+    value = job_glups(ws, n_nodes, args.steps, t_ms * 1e-3)
 
     # stability check of the state that was timed (not timed)
     diag = dom.diagnostics()
@@ -305,13 +318,8 @@ def run_ours(args, case):
     pflbm.pflbm_step(e2e_dom.h, args.steps)
     pflbm.pflbm_read_fields(e2e_dom.h, out_host)
     stream.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": ws * n_nodes * args.steps / e2e_s / 1e9, "unit": "GLUPS",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    e2e = {"value": job_glups(ws, n_nodes, args.steps, e2e_s), "unit": "GLUPS",
            "h2d_bytes_per_step": n_nodes * 4 / args.steps,
            "d2h_bytes_per_step": len(pflbm.FIELDS) * n_nodes * 4 / args.steps}
 
