@@ -19,6 +19,10 @@ in L2 and no dirty line of the flush left for it to write back.  Each step is
 timed with CUDA events on the domain's stream around its single kernel
 launch.
 
+The line also carries "l2_exceeding": the same physics on 2048 x 4096 nodes
+(1.34 GB of state per step, larger than L2), timed over consecutive steps,
+and "cpu_baseline" times the FP64 oracle on all host cores and on one.
+
 Multi-GPU (torchrun, one rank per GPU): every rank advances its own replica
 of the workload, no data-path collective (the instances are independent);
 value = all ranks' node-steps / max over ranks of the time ("scaling":
@@ -185,11 +189,28 @@ def job_glups(ws: int, n_nodes: int, steps: int, seconds: float) -> float:
     return ws * n_nodes * steps / seconds / 1e9
 
 
-def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2):
+def cpu_model() -> str:
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2, threads=None):
     """Oracle steps on the full grid of the workload until `seconds` of CPU
-    work: returns (GLUPS, steps, threads)."""
+    work on `threads` OpenMP threads (all host cores by default): returns
+    (GLUPS, steps, threads)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0)
     s.step(1)  # first step separately (first-step flag), untimed
@@ -342,9 +363,16 @@ def run_ours(args, case):
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        v, n, thr = oracle_sample(case, seconds=args.cpu_seconds)
+        v, n, thr = oracle_sample(case, seconds=0.75 * args.cpu_seconds)
+        v1, n1, _ = oracle_sample(case, seconds=0.25 * args.cpu_seconds, min_steps=1, threads=1)
         cpu = {"value": v, "unit": "GLUPS", "cores": thr, "kind": "oracle",
-               "sample": f"{n} full-grid FP64 oracle steps of {args.workload}"}
+               "sample": f"{n} full-grid FP64 oracle steps of {args.workload}",
+               "value_1thread": v1, "sample_1thread": f"{n1} steps on one thread",
+               "cpu_model": cpu_model()}
+
+    # the same physics on a grid whose state exceeds L2 (8.4 M nodes, 1.34 GB
+    # per step), timed over consecutive steps without flushing
+    l2x = measure_l2_exceeding(args, dev) if ws == 1 and not args.no_l2x else None
 
     line = {
         "metric": "GLUPS (coupled f+h step)", "value": value, "unit": "GLUPS",
@@ -363,10 +391,42 @@ def run_ours(args, case):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    if l2x is not None:
+        line["l2_exceeding"] = l2x
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_l2_exceeding(args, dev, steps=30):
+    """GLUPS and roofline fraction of the step on the 2048 x 4096 rising
+    bubble (same physics as the default workload, state larger than L2)."""
+    import torch
+    from paper_2012_14729_gb300 import pflbm
+    name = "bubble_4096x2048"
+    case = make_case(name, args.form)
+    n = case.nx * case.ny
+    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage, device=dev)
+    dom.set_params(**case.params)
+    dom.init_phi(case.phi0.astype(np.float32))
+    stage = dom.autotune(5)
+    dom.step(max(3, args.warmup))
+    stream = dom.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    dom.step(steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peak, _ = measured_peaks()
+    bpl = BYTES_PER_LUP[args.storage]
+    return {"workload": name, "nx": case.nx, "ny": case.ny, "value": n / (ms * 1e-3) / 1e9,
+            "unit": "GLUPS", "ms_per_step": ms, "steps": steps, "stage": stage,
+            "roofline_frac": bpl * n / (ms * 1e-3) / 1e9 / peak,
+            "l2": f"state {bpl * n / 1e9:.2f} GB per step, larger than L2: consecutive steps",
+            "state_status": dom.diagnostics()["status"]}
 
 
 def main():
@@ -382,6 +442,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-l2x", action="store_true",
+                    help="skip the extra 2048 x 4096 (larger than L2) measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
