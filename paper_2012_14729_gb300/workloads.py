@@ -195,6 +195,30 @@ def batch_instances(n=256, seed=0, sizes=(64, 128, 256, 512)):
     return out
 
 
+def capillary_wave(form="STF1", H=80, h0_frac=0.02, Uc=0.05, rho_ratio=1.0, Re=50.0, We=1.0,
+                   M=0.05, W=4.0):
+    """H x 3H, walls at bottom and top, periodic sides; heavy fluid 1 below
+    the interface y = 1.5 H + h0 cos(k x), k = 2 pi / H, h0 = h0_frac H
+    (Sec. 5.3).  Parameters from the paper's groups Re = 50, We = 1 with
+    Lc = H and a lattice reference velocity Uc; equal kinematic viscosities
+    (the analytic solution assumes them).  The mobility is set directly: the
+    default Pe = 1/Cn would give M = W We / (3 Uc Pe) = 1.33 here, for which
+    the scheme diverges within ten steps; M = 0.05 is Pe = 533."""
+    from . import units
+    Pe = W * We / (3.0 * Uc * M)
+    p = units.lattice_params(Lc=H, Uc=Uc, Re=Re, We=We, Cn=W / H, Pe=Pe, rho_ratio=rho_ratio,
+                             mu_ratio=rho_ratio)
+    p["form"] = form
+    nx, ny = H, 3 * H
+    x, y = _grid(nx, ny)
+    h0 = h0_frac * H
+    # walls at y = -1/2 and ny - 1/2: height Y = y + 1/2 above the bottom wall
+    yi = 1.5 * H - 0.5 + h0 * np.cos(2.0 * math.pi * x / nx)
+    phi0 = np.tanh(2.0 * (yi - y) / W)
+    return Case("capillary_wave", nx, ny, True, p, phi0, 0,
+                {"h0": h0, "k": 2.0 * math.pi / H, "Uc": Uc})
+
+
 def shear_drop(form="STF1", nx=512, ny=256, R=40.0, U=0.01, W=4.0, M=0.05,
                Re=1.0, Ca=0.2):
     """512x256, walls moving at +U (top) and -U (bottom), drop R = 40 at the
