@@ -195,15 +195,18 @@ def batch_instances(n=256, seed=0, sizes=(64, 128, 256, 512)):
     return out
 
 
-def capillary_wave(form="STF1", H=80, h0_frac=0.02, Uc=0.05, rho_ratio=1.0, Re=50.0, We=1.0,
+def capillary_wave(form="STF1", H=80, h0_frac=0.02, Uc=0.01, rho_ratio=1.0, Re=50.0, We=1.0,
                    M=0.05, W=4.0):
     """H x 3H, walls at bottom and top, periodic sides; heavy fluid 1 below
     the interface y = 1.5 H + h0 cos(k x), k = 2 pi / H, h0 = h0_frac H
     (Sec. 5.3).  Parameters from the paper's groups Re = 50, We = 1 with
-    Lc = H and a lattice reference velocity Uc; equal kinematic viscosities
-    (the analytic solution assumes them).  The mobility is set directly: the
-    default Pe = 1/Cn would give M = W We / (3 Uc Pe) = 1.33 here, for which
-    the scheme diverges within ten steps; M = 0.05 is Pe = 533."""
+    Lc = H and a lattice reference velocity Uc (sigma = H Uc^2 / We, nu =
+    Uc H / Re: 0.008 and 0.016 by default); equal kinematic viscosities (the
+    analytic solution assumes them).  The mobility is set directly: the
+    paper's default Pe = 1/Cn gives M = W We / (3 Uc Pe) = 6.7 here, for
+    which the scheme diverges; M = 0.05 is Pe = 2667.  With Uc = 0.02 or
+    0.05 (sigma = 0.032, 0.2) CPF-1 and PF-2 diverge, in the FP64 oracle as
+    on the GPU."""
     from . import units
     Pe = W * We / (3.0 * Uc * M)
     p = units.lattice_params(Lc=H, Uc=Uc, Re=Re, We=We, Cn=W / H, Pe=Pe, rho_ratio=rho_ratio,
