@@ -452,7 +452,7 @@ def main():
             raise SystemExit("the batched workload has no reference arm of its own")
         run_batch(args)
         return
-    if args.workload == "adjoint_shear":
+    if args.workload.startswith("adjoint_shear"):
         if args.impl == "reference":
             raise SystemExit("the adjoint workload has no reference arm of its own")
         run_adjoint(args)
@@ -478,7 +478,11 @@ def run_adjoint(args):
     build.build()
     pflbm.load()
     dev = torch.device("cuda", torch.cuda.current_device())
-    c = wl.shear_drop(args.form)
+    # adjoint_shear: the 512 x 256 configuration; adjoint_shear_x<s>: the same
+    # drop-in-shear physics on an s-times larger grid in each direction (drop
+    # radius and wall speed scaled to keep Re and Ca)
+    s = int(args.workload.rsplit("_x", 1)[1]) if "_x" in args.workload else 1
+    c = wl.shear_drop(args.form, nx=512 * s, ny=256 * s, R=40.0 * s, U=0.01)
     T, every = args.steps, min(200, args.steps)
     stream = torch.cuda.Stream(dev)
     d = pflbm.Domain(c.nx, c.ny, wall_y=True, stream=stream, device=dev).set_params(**c.params)
@@ -517,7 +521,7 @@ def run_adjoint(args):
         "unit": "GLUPS", "n_gpus": 1, "steps": T, "warmup": args.warmup,
         "ms_per_step": t_fwd / T, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "adjoint_shear", "nx": c.nx, "ny": c.ny, "form": args.form,
+        "config": {"workload": args.workload, "nx": c.nx, "ny": c.ny, "form": args.form,
                    "ckpt_every": every},
         "adjoint": {"gradient_run_ms": t_adj, "forward_ms": t_fwd,
                     "cost_over_forward": t_adj / t_fwd,
