@@ -112,16 +112,19 @@ __device__ __forceinline__ void acc_add(double* acc, double v0, double v1, doubl
   const int k = y * A.g.nx + (live ? x : 0);                  \
   (void)n;
 #define TP(pl) (A.tape + (size_t)(pl) * n)
-#define AI(pl) (A.ain + (size_t)(pl) * n)
-#define AO(pl) (A.aout + (size_t)(pl) * n)
+#define AI(pl) (A.ain + (size_t)(kAdjScalar + (pl)) * n)
+#define AO(pl) (A.aout + (size_t)(kAdjScalar + (pl)) * n)
+#define SI(m) (reinterpret_cast<const float4*>(A.ain)[m])
+#define SO(m) (reinterpret_cast<float4*>(A.aout)[m])
 #define WK(pl) (A.W + (size_t)(pl) * n)
 
 // Full adjoint of pre-collision population i at node m of step t + 1.
-__device__ __forceinline__ float fb_full(const AdjArgs& A, int n, int i, int m) {
-  return AI(AP_F0 + i)[m] + AI(AP_SB)[m] + qcx(i) * AI(AP_JX)[m] + qcy(i) * AI(AP_JY)[m];
+// (s: the node's scalar block SB, JX, JY, PHI, read as one 16-byte load)
+__device__ __forceinline__ float fb_full(const AdjArgs& A, int n, int i, int m, float4 s) {
+  return AI(AP_F0 + i)[m] + s.x + qcx(i) * s.y + qcy(i) * s.z;
 }
-__device__ __forceinline__ float hb_full(const AdjArgs& A, int n, int i, int m) {
-  return AI(AP_H0 + i)[m] + AI(AP_PHI)[m];
+__device__ __forceinline__ float hb_full(const AdjArgs& A, int n, int i, int m, float4 s) {
+  return AI(AP_H0 + i)[m] + s.w;
 }
 
 // streaming transpose + collision transpose (+ bounce-back terms); built for
@@ -155,16 +158,18 @@ __global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
       float fpb, hpb;
       if (g.wall && (yn < 0 || yn >= g.ny)) {
         const int o = qopp(i);
-        fpb = fb_full(A, n, o, k);
-        hpb = hb_full(A, n, o, k);
+        const float4 sk = SI(k);
+        fpb = fb_full(A, n, o, k, sk);
+        hpb = hb_full(A, n, o, k, sk);
         const float cu = qcx(i) * (yn < 0 ? P.uwb : P.uwt);
         rhob += -2.0f * qw(i) * cu * fpb;
         phib += -6.0f * qw(i) * cu * hpb;
       } else {
         if (!g.wall) yn = yn < 0 ? yn + g.ny : (yn >= g.ny ? yn - g.ny : yn);
         const int m = yn * g.nx + xn;
-        fpb = fb_full(A, n, i, m);
-        hpb = hb_full(A, n, i, m);
+        const float4 sm = SI(m);
+        fpb = fb_full(A, n, i, m, sm);
+        hpb = hb_full(A, n, i, m, sm);
       }
       const float cu = qcx(i) * ux + qcy(i) * uy;
       const float s = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
@@ -281,9 +286,8 @@ __global__ void __launch_bounds__(kAB) k_adj_mid(const AdjArgs A) {
     const float uyb = WK(B_UY)[k] + phi * pyb + Ry * c6 * Pb;
     float Gxb = WK(B_GX)[k] + P.drho_half * (ux * c6 * Pb);
     float Gyb = WK(B_GY)[k] + P.drho_half * (uy * c6 * Pb);
-    AO(AP_SB)[k] = Pb;
-    AO(AP_JX)[k] = 3.0f * uxb * irho;
-    AO(AP_JY)[k] = 3.0f * uyb * irho;
+    // (PHI, the w component, is written by the finishing kernel)
+    SO(k) = make_float4(Pb, 3.0f * uxb * irho, 3.0f * uyb * irho, 0.0f);
     const float Fxb = WK(B_FX)[k] + 0.5f * uxb * irho;  // adjoint of F_sf
     const float Fyb = WK(B_FY)[k] + 0.5f * uyb * irho;
     float rhob = WK(B_RHO)[k] - (ux * uxb + uy * uyb) * irho;
@@ -430,9 +434,9 @@ __global__ void __launch_bounds__(kAB) k_adj_finish(const AdjArgs A) {
   ADJ_NODE
   if (!live) return;
   const Geo& g = A.g;
-  AO(AP_PHI)[k] = WK(B_PHI)[k] + stencil_T<false>(WK(B_GX), g, x, y, 0, 1.0f) +
-                  stencil_T<false>(WK(B_GY), g, x, y, 1, 1.0f) +
-                  stencil_T<true>(WK(B_L), g, x, y, 0, 1.0f);
+  reinterpret_cast<float*>(A.aout)[4 * k + 3] =  // the PHI (w) component of SO(k)
+      WK(B_PHI)[k] + stencil_T<false>(WK(B_GX), g, x, y, 0, 1.0f) +
+      stencil_T<false>(WK(B_GY), g, x, y, 1, 1.0f) + stencil_T<true>(WK(B_L), g, x, y, 0, 1.0f);
 }
 
 // Reverse of one step: adjoint state at t + 1 (A.ain) -> at t (A.aout), with
@@ -455,10 +459,11 @@ __global__ void __launch_bounds__(kAB) k_adj_init_pt(const AdjArgs A, const floa
     const float phi = phi0[k];
     const float L = lapfw(phi0, A.g, x, y);
     const float mu = P.beta4 * phi * ((phi - 1.0f) * (phi + 1.0f)) - P.kappa * L;
-    const float hb0 = hb_full(A, n, 0, k);
+    const float4 sk = SI(k);
+    const float hb0 = hb_full(A, n, 0, k, sk);
     float hsum = (qw(0) - 1.0f) * hb0;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) hsum += qw(i) * hb_full(A, n, i, k);
+    for (int i = 1; i < 9; ++i) hsum += qw(i) * hb_full(A, n, i, k, sk);
     const float mub = P.eta * hsum;
     de = (double)(mu * hsum);
     db = (double)(phi * (phi * phi - 1.0f) * mub);

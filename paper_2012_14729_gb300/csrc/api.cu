@@ -729,7 +729,7 @@ bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
   off = align_up(off + (size_t)kWorkPlanes * n * 4);
   for (int b = 0; b < 2; ++b) {
     L->adj[b] = off;
-    off = align_up(off + (size_t)kAdjPlanes * n * 4);
+    off = align_up(off + (size_t)(kAdjScalar + kAdjPlanes) * n * 4);
   }
   L->acc = off;
   off = align_up(off + 4 * sizeof(double));
@@ -837,10 +837,10 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
   int cur = 0;
   float* adj[2] = {reinterpret_cast<float*>(S + L.adj[0]), reinterpret_cast<float*>(S + L.adj[1])};
   double* acc = reinterpret_cast<double*>(S + L.acc);
-  e = cudaMemsetAsync(adj[0], 0, (size_t)kAdjPlanes * n * 4, d->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(adj[0] + (size_t)AP_PHI * n, dJ_dphiT, n * 4, cudaMemcpyDeviceToDevice,
-                        d->stream);
+  e = cudaMemsetAsync(adj[0], 0, (size_t)(kAdjScalar + kAdjPlanes) * n * 4, d->stream);
+  if (e == cudaSuccess)  // dJ/dphi_T into the PHI (4th) float of each node's scalar block
+    e = cudaMemcpy2DAsync(adj[0] + 3, 4 * sizeof(float), dJ_dphiT, sizeof(float), sizeof(float),
+                          n, cudaMemcpyDeviceToDevice, d->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), d->stream);
   if (e != cudaSuccess) return fail("adjoint setup");
 

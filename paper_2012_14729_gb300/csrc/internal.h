@@ -101,11 +101,13 @@ constexpr int kBoxRowsH = kTY + 6;  // phi is needed on the tile + 3 ring
 constexpr int kBoxRowsF = kTY + 2;  // f on the tile + 1 ring
 
 // Adjoint of one step (adjoint.cu), float32 planes of n = nx ny nodes.
-// Adjoint state between reverse steps: the adjoint of the pre-collision
-// populations is kept as per-population parts plus per-node scalars added to
-// every population when it is read (f_i: AP_F0 + i + AP_SB + c_i . AP_J;
-// h_i: AP_H0 + i + AP_PHI), and the adjoint of (phi u)^{t-1}.
-enum AdjPlane { AP_F0 = 0, AP_H0 = 9, AP_SB = 18, AP_JX, AP_JY, AP_PHI, AP_QX, AP_QY, kAdjPlanes };
+// Adjoint state between reverse steps: first one float4 per node of scalars
+// (SB, JX, JY, PHI) that are added to every population when it is read (f_i:
+// AP_F0 + i + SB + c_i . (JX, JY); h_i: AP_H0 + i + PHI), then the
+// per-population planes and the adjoint of (phi u)^{t-1}; plane p starts at
+// float offset (kAdjScalar + p) n.
+enum AdjPlane { AP_F0 = 0, AP_H0 = 9, AP_QX = 18, AP_QY, kAdjPlanes };
+constexpr int kAdjScalar = 4;  // floats of the per-node scalar block
 // Work planes of one reverse step.
 enum WorkPlane {
   B_PHI, B_RHO, B_UX, B_UY, B_P, B_FX, B_FY, B_GX, B_GY, B_MU, B_DIV, B_DTX, B_DTY, B_L, B_W0,
@@ -119,8 +121,8 @@ struct AdjArgs {
   Phys p;
   int form, first;
   const float* tape;  // [kTapePlanes][n] recorded by the taping step at t
-  const float* ain;   // [kAdjPlanes][n] adjoint state at t + 1
-  float* aout;        // [kAdjPlanes][n] adjoint state at t
+  const float* ain;   // adjoint state at t + 1: float4 [n], then [kAdjPlanes][n]
+  float* aout;        // adjoint state at t, same layout
   float* W;           // [kWorkPlanes][n]
   double* acc;        // [4]: d/d(4 beta), d/d kappa, d/d eta, direct d/d sigma
 };
