@@ -21,6 +21,10 @@
 // added to four accumulators.
 #include "step_kernel.cuh"
 
+#ifndef ADJ_TAIL_FUSED_MAX
+#define ADJ_TAIL_FUSED_MAX 262144
+#endif
+
 namespace pflbm {
 
 namespace {
@@ -235,196 +239,344 @@ __global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
   acc_add(A.acc, 0.0, 0.0, deta, 0.0);
 }
 
+// Values of the middle and late stages at one node.
+struct Tail {
+  float phib, Gxb, Gyb, mub, Lb, w0, w1, w2;
+};
+
 // div(phi u) and d_t(phi u) = p - q, the incoming adjoint of (phi u)^t, then
 // p = phi u, P = S + u.R/6, u = (3 j + F/2)/rho, F = F_sf + (rho - rho0) g,
-// rho(phi), and the pointwise part of the force of the form.  Leaves in W0..W2
-// what the force's stencil transposes read.
-__global__ void __launch_bounds__(kAB) k_adj_mid(const AdjArgs A) {
-  ADJ_NODE
+// rho(phi), and the pointwise part of the force of the form; leaves in
+// w0..w2 what the force's stencil transposes read.  The node's outputs to the
+// adjoint state (q and the scalar block) are written when `own`.
+__device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, int k, bool own,
+                                         double& dk, double& ds) {
   const Phys& P = A.p;
   const Geo& g = A.g;
+  const float* divb = WK(B_DIV);
+  // p_x is read as parity -1 with an additive 2 u_w phi at the wall ghosts,
+  // p_y with parity -1; periodic wraps
+  float pxb = stencil_T<false>(divb, g, x, y, 0, -1.0f);
+  float pyb = stencil_T<false>(divb, g, x, y, 1, -1.0f);
+  Tail o;
+  o.phib = WK(B_PHI)[k];
+  if (g.wall && (y == 0 || y == g.ny - 1)) {
+    // ghost adjoint of p_x at (x, -1) or (x, ny): nodes of this row whose
+    // stencil reads it; its 2 u_w phi(x, row) part goes to phi
+    const int cyw = y == 0 ? -1 : 1;
+    float ga = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if (qcy(i) == cyw) ga += 3.0f * qw(i) * qcx(i) * divb[y * g.nx + wx(g, x - qcx(i))];
+    o.phib += 2.0f * (y == 0 ? P.uwb : P.uwt) * ga;
+  }
+  pxb += AI(AP_QX)[k];
+  pyb += AI(AP_QY)[k];
+  const float dtxb = A.first ? 0.0f : WK(B_DTX)[k], dtyb = A.first ? 0.0f : WK(B_DTY)[k];
+  pxb += dtxb;
+  pyb += dtyb;
+  // macroscopic relations
+  const float phi = TP(TP_PHI)[k], ux = TP(TP_UX)[k], uy = TP(TP_UY)[k];
+  const float gx = TP(TP_GX)[k], gy = TP(TP_GY)[k];
+  constexpr float c6 = 1.0f / 6.0f;
+  const float rho = P.rho_mid + P.drho_half * phi;
+  const float irho = 1.0f / rho;
+  const float Rx = P.drho_half * gx, Ry = P.drho_half * gy;
+  const float Pb = WK(B_P)[k];
+  o.phib += pxb * ux + pyb * uy;
+  const float uxb = WK(B_UX)[k] + phi * pxb + Rx * c6 * Pb;
+  const float uyb = WK(B_UY)[k] + phi * pyb + Ry * c6 * Pb;
+  o.Gxb = WK(B_GX)[k] + P.drho_half * (ux * c6 * Pb);
+  o.Gyb = WK(B_GY)[k] + P.drho_half * (uy * c6 * Pb);
+  if (own) {
+    AO(AP_QX)[k] = -dtxb;
+    AO(AP_QY)[k] = -dtyb;
+    // (PHI, the w component, is written by the finishing stage)
+    SO(k) = make_float4(Pb, 3.0f * uxb * irho, 3.0f * uyb * irho, 0.0f);
+  }
+  const float Fxb = WK(B_FX)[k] + 0.5f * uxb * irho;  // adjoint of F_sf
+  const float Fyb = WK(B_FY)[k] + 0.5f * uyb * irho;
+  float rhob = WK(B_RHO)[k] - (ux * uxb + uy * uyb) * irho;
+  rhob += P.gx * Fxb + P.gy * Fyb;
+  o.phib += P.drho_half * rhob;
+  // pointwise part of the force
+  o.mub = WK(B_MU)[k];
+  o.Lb = o.w0 = o.w1 = o.w2 = 0.0f;
+  const float a0 = TP(TP_A0)[k], a1 = TP(TP_A1)[k];
+  switch (A.form) {
+    case kSTF1:
+    case kSTF2:  // F_sf = kappa (a0, a1) / kappa: the tape holds F_sf
+      dk += (double)((Fxb * a0 + Fyb * a1) * (1.0f / P.kappa));
+      o.w0 = Fxb;
+      o.w1 = Fyb;
+      break;
+    case kCPF1:  // F = -phi grad mu, tape: grad mu
+      o.phib += -(a0 * Fxb + a1 * Fyb);
+      o.w0 = -phi * Fxb;
+      o.w1 = -phi * Fyb;
+      break;
+    case kCPF2: {
+      const float mu = TP(TP_MU)[k];
+      o.mub += gx * Fxb + gy * Fyb;
+      o.Gxb += mu * Fxb;
+      o.Gyb += mu * Fyb;
+      break;
+    }
+    case kPF1: {
+      const float L = TP(TP_L)[k];
+      o.Gxb += -P.kappa * L * Fxb;
+      o.Gyb += -P.kappa * L * Fyb;
+      o.Lb = -P.kappa * (gx * Fxb + gy * Fyb);
+      dk += (double)(-(gx * Fxb + gy * Fyb) * L);
+      break;
+    }
+    case kPF2:  // F = kappa phi grad lap phi, tape: grad lap phi
+      o.phib += P.kappa * (a0 * Fxb + a1 * Fyb);
+      dk += (double)(phi * (a0 * Fxb + a1 * Fyb));
+      o.w0 = P.kappa * phi * Fxb;
+      o.w1 = P.kappa * phi * Fyb;
+      break;
+    default: {  // CSF, tape: div n
+      const float divn = a0;
+      const float a = sqrtf(gx * gx + gy * gy);
+      const float GF = gx * Fxb + gy * Fyb;
+      if (A.form == kCSF1) {
+        o.Gxb += -P.kappa * a * divn * Fxb;
+        o.Gyb += -P.kappa * a * divn * Fyb;
+        const float ab = -P.kappa * divn * GF;
+        o.w2 = -P.kappa * a * GF;
+        dk += (double)(-GF * a * divn);
+        if (a > 0.0f) {
+          const float ia = 1.0f / a;
+          o.Gxb += ab * gx * ia;
+          o.Gyb += ab * gy * ia;
+        }
+      } else {
+        o.Gxb += -P.half_sigma * divn * Fxb;
+        o.Gyb += -P.half_sigma * divn * Fyb;
+        o.w2 = -P.half_sigma * GF;
+        ds += (double)(-0.5f * GF * divn);
+      }
+    }
+  }
+  return o;
+}
+
+// Stencil part of the force adjoint, then mu = 4 beta phi (phi^2 - 1) - kappa
+// lap phi, at node k with its middle-stage values v; st(field, axis, parity)
+// is the transposed first-derivative stencil of w0, w1 or w2 (field 0, 1, 2).
+template <class ST>
+__device__ __forceinline__ void late_node(const AdjArgs& A, int n, int k, Tail& v, const ST& st,
+                                          double& db, double& dk) {
+  const Phys& P = A.p;
+  const float gx = TP(TP_GX)[k], gy = TP(TP_GY)[k], phi = TP(TP_PHI)[k];
+  switch (A.form) {
+    case kSTF1:
+    case kSTF2: {
+      float txx = -P.kappa * st(0, 0, 1.0f);
+      const float txy = -P.kappa * (st(0, 1, -1.0f) + st(1, 0, -1.0f));
+      float tyy = -P.kappa * st(1, 1, 1.0f);
+      if (A.form == kSTF2) {
+        const float g2b = P.kappa * (st(0, 0, 1.0f) + st(1, 1, 1.0f));
+        txx += g2b;
+        tyy += g2b;
+      }
+      v.Gxb += 2.0f * gx * txx + gy * txy;
+      v.Gyb += gx * txy + 2.0f * gy * tyy;
+      break;
+    }
+    case kCPF1:
+      v.mub += st(0, 0, 1.0f) + st(1, 1, 1.0f);
+      break;
+    case kPF2:
+      v.Lb += st(0, 0, 1.0f) + st(1, 1, 1.0f);
+      break;
+    case kCSF1:
+    case kCSF2: {
+      const float nxb = st(2, 0, 1.0f);
+      const float nyb = st(2, 1, -1.0f);
+      const float ir = rsqrtf(gx * gx + gy * gy + P.eps2);
+      const float gn = gx * nxb + gy * nyb, ir3 = ir * ir * ir;
+      v.Gxb += nxb * ir - gx * gn * ir3;
+      v.Gyb += nyb * ir - gy * gn * ir3;
+      break;
+    }
+    default:
+      break;
+  }
+  v.phib += P.beta4 * (3.0f * phi * phi - 1.0f) * v.mub;
+  v.Lb += -P.kappa * v.mub;
+  db += (double)(phi * (phi * phi - 1.0f) * v.mub);
+  dk += (double)(-TP(TP_L)[k] * v.mub);
+}
+
+// Transposed stencils on a shared-memory tile of row stride S: node at local
+// index c, domain row y (the wall rule of stencil_T, periodic seams already
+// resolved by the tile's layout).
+template <bool LAP, int S>
+__device__ __forceinline__ float stencil_T_tile(const float* b, int c, int y, const Geo& g,
+                                                int axis, float parity) {
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const int cxi = qcx(i), cyi = qcy(i);
+    const int cc = LAP ? 1 : (axis == 0 ? cxi : cyi);
+    if (cc == 0) continue;
+    const float coef = LAP ? 6.0f * qw(i) : 3.0f * qw(i) * cc;
+    if (g.wall) {
+      const int ys = y - cyi;
+      if (ys >= 0 && ys < g.ny) s += coef * b[c - cxi - cyi * S];
+      if ((y == 0 && cyi == -1) || (y == g.ny - 1 && cyi == 1)) s += parity * coef * b[c - cxi];
+    } else {
+      s += coef * b[c - cxi - cyi * S];
+    }
+  }
+  if (LAP) s -= (10.0f / 3.0f) * b[c];
+  return s;
+}
+
+// The three stages after the collision transpose, fused over a 32 x 8 tile:
+// the middle stage on the tile + 2 ring, the late stage on the tile + 1 ring
+// (its stencils read the middle stage's w0..w2 in shared memory), the
+// finishing transposes of grad phi and lap phi on the tile.  A ring node
+// outside the domain beyond a wall is skipped (no stencil reads it); every
+// parameter gradient term comes from the tile's own nodes.
+constexpr int kTW = 32, kTH = 8, kTS = kTW + 4, kTN = kTS * (kTH + 4);
+__global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
+  const int n = A.g.nx * A.g.ny;
+  const Geo& g = A.g;
+  __shared__ float sw[3][kTN];   // w0, w1, w2
+  __shared__ float sv[5][kTN];   // phib, Gxb, Gyb, mub, Lb
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+  double dk = 0.0, ds = 0.0, db = 0.0;
+  // node (lx, ly) of the tile + 2 ring: domain coordinates, or false beyond a wall
+  auto node = [&](int lx, int ly, int& x, int& y) {
+    x = wx(g, x0 - 2 + lx);
+    y = y0 - 2 + ly;
+    if (g.wall) return y >= 0 && y < g.ny;
+    y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+    return true;
+  };
+  auto owned = [&](int lx, int ly) {
+    return lx >= 2 && lx < kTW + 2 && ly >= 2 && ly < kTH + 2 && x0 + lx - 2 < g.nx &&
+           y0 + ly - 2 < g.ny;
+  };
+  for (int c = threadIdx.x; c < kTN; c += 256) {
+    const int ly = c / kTS, lx = c - ly * kTS;
+    int x, y;
+    if (!node(lx, ly, x, y)) continue;
+    const bool own = owned(lx, ly);
+    double dkn = 0.0, dsn = 0.0;
+    const Tail t = mid_node(A, n, x, y, y * g.nx + x, own, dkn, dsn);
+    if (own) {
+      dk += dkn;
+      ds += dsn;
+    }
+    sw[0][c] = t.w0;
+    sw[1][c] = t.w1;
+    sw[2][c] = t.w2;
+    sv[0][c] = t.phib;
+    sv[1][c] = t.Gxb;
+    sv[2][c] = t.Gyb;
+    sv[3][c] = t.mub;
+    sv[4][c] = t.Lb;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kTN; c += 256) {
+    const int ly = c / kTS, lx = c - ly * kTS;
+    if (lx < 1 || lx > kTW + 2 || ly < 1 || ly > kTH + 2) continue;  // tile + 1 ring
+    int x, y;
+    if (!node(lx, ly, x, y)) continue;
+    Tail v;
+    v.phib = sv[0][c];
+    v.Gxb = sv[1][c];
+    v.Gyb = sv[2][c];
+    v.mub = sv[3][c];
+    v.Lb = sv[4][c];
+    const auto st = [&](int f, int axis, float parity) {
+      return stencil_T_tile<false, kTS>(sw[f], c, y, g, axis, parity);
+    };
+    double dbn = 0.0, dkn = 0.0;
+    late_node(A, n, y * g.nx + x, v, st, dbn, dkn);
+    if (owned(lx, ly)) {
+      db += dbn;
+      dk += dkn;
+    }
+    sv[0][c] = v.phib;  // the late stage reads only w0..w2 of other nodes
+    sv[1][c] = v.Gxb;
+    sv[2][c] = v.Gyb;
+    sv[4][c] = v.Lb;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kTN; c += 256) {
+    const int ly = c / kTS, lx = c - ly * kTS;
+    if (!owned(lx, ly)) continue;
+    int x, y;
+    node(lx, ly, x, y);
+    const int k = y * g.nx + x;
+    reinterpret_cast<float*>(A.aout)[4 * k + 3] =  // the PHI (w) component of SO(k)
+        sv[0][c] + stencil_T_tile<false, kTS>(sv[1], c, y, g, 0, 1.0f) +
+        stencil_T_tile<false, kTS>(sv[2], c, y, g, 1, 1.0f) +
+        stencil_T_tile<true, kTS>(sv[4], c, y, g, 0, 1.0f);
+  }
+  // one FP64 block reduction of the four accumulators (256 threads)
+  __shared__ double red[8][4];
+  double v4[4] = {db, dk, 0.0, ds};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v4[q] += __shfl_down_sync(0xffffffffu, v4[q], o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[w][q] = v4[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int j = 0; j < 8; ++j) s += red[j][threadIdx.x];
+    if (s != 0.0) atomicAdd(&A.acc[threadIdx.x], s);
+  }
+}
+
+// The same three stages as separate one-thread-per-node kernels over the
+// whole grid, exchanging their values through the work planes.
+__global__ void __launch_bounds__(kAB) k_adj_mid(const AdjArgs A) {
+  ADJ_NODE
   double dk = 0.0, ds = 0.0;
   if (live) {
-    const float* divb = WK(B_DIV);
-    // p_x is read as parity -1 with an additive 2 u_w phi at the wall ghosts,
-    // p_y with parity -1; periodic wraps
-    float pxb = stencil_T<false>(divb, g, x, y, 0, -1.0f);
-    float pyb = stencil_T<false>(divb, g, x, y, 1, -1.0f);
-    float phib = WK(B_PHI)[k];
-    if (g.wall && (y == 0 || y == g.ny - 1)) {
-      // ghost adjoint of p_x at (x, -1) or (x, ny): nodes of this row whose
-      // stencil reads it; its 2 u_w phi(x, row) part goes to phi
-      const int cyw = y == 0 ? -1 : 1;
-      float ga = 0.0f;
-#pragma unroll
-      for (int i = 1; i < 9; ++i)
-        if (qcy(i) == cyw) ga += 3.0f * qw(i) * qcx(i) * divb[y * g.nx + wx(g, x - qcx(i))];
-      phib += 2.0f * (y == 0 ? P.uwb : P.uwt) * ga;
-    }
-    pxb += AI(AP_QX)[k];
-    pyb += AI(AP_QY)[k];
-    if (!A.first) {
-      const float dtxb = WK(B_DTX)[k], dtyb = WK(B_DTY)[k];
-      pxb += dtxb;
-      pyb += dtyb;
-      AO(AP_QX)[k] = -dtxb;
-      AO(AP_QY)[k] = -dtyb;
-    } else {
-      AO(AP_QX)[k] = 0.0f;
-      AO(AP_QY)[k] = 0.0f;
-    }
-    // macroscopic relations
-    const float phi = TP(TP_PHI)[k], ux = TP(TP_UX)[k], uy = TP(TP_UY)[k];
-    const float gx = TP(TP_GX)[k], gy = TP(TP_GY)[k];
-    constexpr float c6 = 1.0f / 6.0f;
-    const float rho = P.rho_mid + P.drho_half * phi;
-    const float irho = 1.0f / rho;
-    const float Rx = P.drho_half * gx, Ry = P.drho_half * gy;
-    const float Pb = WK(B_P)[k];
-    phib += pxb * ux + pyb * uy;
-    const float uxb = WK(B_UX)[k] + phi * pxb + Rx * c6 * Pb;
-    const float uyb = WK(B_UY)[k] + phi * pyb + Ry * c6 * Pb;
-    float Gxb = WK(B_GX)[k] + P.drho_half * (ux * c6 * Pb);
-    float Gyb = WK(B_GY)[k] + P.drho_half * (uy * c6 * Pb);
-    // (PHI, the w component, is written by the finishing kernel)
-    SO(k) = make_float4(Pb, 3.0f * uxb * irho, 3.0f * uyb * irho, 0.0f);
-    const float Fxb = WK(B_FX)[k] + 0.5f * uxb * irho;  // adjoint of F_sf
-    const float Fyb = WK(B_FY)[k] + 0.5f * uyb * irho;
-    float rhob = WK(B_RHO)[k] - (ux * uxb + uy * uyb) * irho;
-    rhob += P.gx * Fxb + P.gy * Fyb;
-    phib += P.drho_half * rhob;
-    // pointwise part of the force
-    float mub = WK(B_MU)[k], Lb = 0.0f, w0 = 0.0f, w1 = 0.0f, w2 = 0.0f;
-    const float a0 = TP(TP_A0)[k], a1 = TP(TP_A1)[k];
-    switch (A.form) {
-      case kSTF1:
-      case kSTF2:  // F_sf = kappa (a0, a1) / kappa: the tape holds F_sf
-        dk = (double)((Fxb * a0 + Fyb * a1) * (1.0f / P.kappa));
-        w0 = Fxb;
-        w1 = Fyb;
-        break;
-      case kCPF1:  // F = -phi grad mu, tape: grad mu
-        phib += -(a0 * Fxb + a1 * Fyb);
-        w0 = -phi * Fxb;
-        w1 = -phi * Fyb;
-        break;
-      case kCPF2: {
-        const float mu = TP(TP_MU)[k];
-        mub += gx * Fxb + gy * Fyb;
-        Gxb += mu * Fxb;
-        Gyb += mu * Fyb;
-        break;
-      }
-      case kPF1: {
-        const float L = TP(TP_L)[k];
-        Gxb += -P.kappa * L * Fxb;
-        Gyb += -P.kappa * L * Fyb;
-        Lb = -P.kappa * (gx * Fxb + gy * Fyb);
-        dk = (double)(-(gx * Fxb + gy * Fyb) * L);
-        break;
-      }
-      case kPF2:  // F = kappa phi grad lap phi, tape: grad lap phi
-        phib += P.kappa * (a0 * Fxb + a1 * Fyb);
-        dk = (double)(phi * (a0 * Fxb + a1 * Fyb));
-        w0 = P.kappa * phi * Fxb;
-        w1 = P.kappa * phi * Fyb;
-        break;
-      default: {  // CSF, tape: div n
-        const float divn = a0;
-        const float a = sqrtf(gx * gx + gy * gy);
-        const float GF = gx * Fxb + gy * Fyb;
-        float divnb;
-        if (A.form == kCSF1) {
-          Gxb += -P.kappa * a * divn * Fxb;
-          Gyb += -P.kappa * a * divn * Fyb;
-          const float ab = -P.kappa * divn * GF;
-          divnb = -P.kappa * a * GF;
-          dk = (double)(-GF * a * divn);
-          if (a > 0.0f) {
-            const float ia = 1.0f / a;
-            Gxb += ab * gx * ia;
-            Gyb += ab * gy * ia;
-          }
-        } else {
-          Gxb += -P.half_sigma * divn * Fxb;
-          Gyb += -P.half_sigma * divn * Fyb;
-          divnb = -P.half_sigma * GF;
-          ds = (double)(-0.5f * GF * divn);
-        }
-        w2 = divnb;
-      }
-    }
-    WK(B_PHI)[k] = phib;
-    WK(B_GX)[k] = Gxb;
-    WK(B_GY)[k] = Gyb;
-    WK(B_MU)[k] = mub;
-    WK(B_L)[k] = Lb;
-    WK(B_W0)[k] = w0;
-    WK(B_W1)[k] = w1;
-    WK(B_W2)[k] = w2;
+    const Tail t = mid_node(A, n, x, y, k, true, dk, ds);
+    WK(B_PHI)[k] = t.phib;
+    WK(B_GX)[k] = t.Gxb;
+    WK(B_GY)[k] = t.Gyb;
+    WK(B_MU)[k] = t.mub;
+    WK(B_L)[k] = t.Lb;
+    WK(B_W0)[k] = t.w0;
+    WK(B_W1)[k] = t.w1;
+    WK(B_W2)[k] = t.w2;
   }
   acc_add(A.acc, 0.0, dk, 0.0, ds);
 }
 
-// stencil part of the force adjoint, then mu = 4 beta phi (phi^2 - 1) - kappa lap phi
 __global__ void __launch_bounds__(kAB) k_adj_late(const AdjArgs A) {
   ADJ_NODE
-  const Geo& g = A.g;
-  const Phys& P = A.p;
   double db = 0.0, dk = 0.0;
   if (live) {
-    const float gx = TP(TP_GX)[k], gy = TP(TP_GY)[k], phi = TP(TP_PHI)[k];
-    float Gxb = WK(B_GX)[k], Gyb = WK(B_GY)[k], mub = WK(B_MU)[k], Lb = WK(B_L)[k];
-    float phib = WK(B_PHI)[k];
-    switch (A.form) {
-      case kSTF1:
-      case kSTF2: {
-        const float* fxb = WK(B_W0);
-        const float* fyb = WK(B_W1);
-        float txx = -P.kappa * stencil_T<false>(fxb, g, x, y, 0, 1.0f);
-        const float txy = -P.kappa * (stencil_T<false>(fxb, g, x, y, 1, -1.0f) +
-                                      stencil_T<false>(fyb, g, x, y, 0, -1.0f));
-        float tyy = -P.kappa * stencil_T<false>(fyb, g, x, y, 1, 1.0f);
-        if (A.form == kSTF2) {
-          const float g2b = P.kappa * (stencil_T<false>(fxb, g, x, y, 0, 1.0f) +
-                                       stencil_T<false>(fyb, g, x, y, 1, 1.0f));
-          txx += g2b;
-          tyy += g2b;
-        }
-        Gxb += 2.0f * gx * txx + gy * txy;
-        Gyb += gx * txy + 2.0f * gy * tyy;
-        break;
-      }
-      case kCPF1:
-        mub += stencil_T<false>(WK(B_W0), g, x, y, 0, 1.0f) +
-               stencil_T<false>(WK(B_W1), g, x, y, 1, 1.0f);
-        break;
-      case kPF2:
-        Lb += stencil_T<false>(WK(B_W0), g, x, y, 0, 1.0f) +
-              stencil_T<false>(WK(B_W1), g, x, y, 1, 1.0f);
-        break;
-      case kCSF1:
-      case kCSF2: {
-        const float* divnb = WK(B_W2);
-        const float nxb = stencil_T<false>(divnb, g, x, y, 0, 1.0f);
-        const float nyb = stencil_T<false>(divnb, g, x, y, 1, -1.0f);
-        const float ir = rsqrtf(gx * gx + gy * gy + P.eps2);
-        const float gn = gx * nxb + gy * nyb, ir3 = ir * ir * ir;
-        Gxb += nxb * ir - gx * gn * ir3;
-        Gyb += nyb * ir - gy * gn * ir3;
-        break;
-      }
-      default:
-        break;
-    }
-    phib += P.beta4 * (3.0f * phi * phi - 1.0f) * mub;
-    Lb += -P.kappa * mub;
-    db = (double)(phi * (phi * phi - 1.0f) * mub);
-    dk = (double)(-TP(TP_L)[k] * mub);
-    WK(B_PHI)[k] = phib;
-    WK(B_GX)[k] = Gxb;
-    WK(B_GY)[k] = Gyb;
-    WK(B_L)[k] = Lb;
+    const Geo& g = A.g;
+    Tail v;
+    v.phib = WK(B_PHI)[k];
+    v.Gxb = WK(B_GX)[k];
+    v.Gyb = WK(B_GY)[k];
+    v.mub = WK(B_MU)[k];
+    v.Lb = WK(B_L)[k];
+    const float* w[3] = {WK(B_W0), WK(B_W1), WK(B_W2)};
+    const auto st = [&](int f, int axis, float parity) {
+      return stencil_T<false>(w[f], g, x, y, axis, parity);
+    };
+    late_node(A, n, k, v, st, db, dk);
+    WK(B_PHI)[k] = v.phib;
+    WK(B_GX)[k] = v.Gxb;
+    WK(B_GY)[k] = v.Gyb;
+    WK(B_L)[k] = v.Lb;
   }
   acc_add(A.acc, db, dk, 0.0, 0.0);
 }
@@ -439,14 +591,27 @@ __global__ void __launch_bounds__(kAB) k_adj_finish(const AdjArgs A) {
       stencil_T<false>(WK(B_GY), g, x, y, 1, 1.0f) + stencil_T<true>(WK(B_L), g, x, y, 0, 1.0f);
 }
 
+// Grids up to this many nodes run the three stages after the collision
+// transpose as one tiled kernel (fewer launches where every kernel is
+// latency-bound); larger grids run them as three kernels (no ring
+// recomputation where the stages are bound by their bytes).  Measured on the
+// drop in shear: fused 20.2 vs 22.1 ms at 131 072 nodes, 68.3 vs 65.6 ms at
+// 524 288 nodes, 229 vs 216 ms at 2 097 152 nodes.
+constexpr long long kTailFusedMaxNodes = ADJ_TAIL_FUSED_MAX;
+
 // Reverse of one step: adjoint state at t + 1 (A.ain) -> at t (A.aout), with
 // the tape of step t.
 cudaError_t launch_adjoint_step(const AdjArgs& A, cudaStream_t s) {
   const dim3 grid((A.g.nx + kAB - 1) / kAB, A.g.ny);
   k_adj_collide<<<grid, kAB, 0, s>>>(A);
-  k_adj_mid<<<grid, kAB, 0, s>>>(A);
-  k_adj_late<<<grid, kAB, 0, s>>>(A);
-  k_adj_finish<<<grid, kAB, 0, s>>>(A);
+  if ((long long)A.g.nx * A.g.ny <= kTailFusedMaxNodes) {
+    const dim3 tiles((A.g.nx + kTW - 1) / kTW, (A.g.ny + kTH - 1) / kTH);
+    k_adj_tail<<<tiles, 256, 0, s>>>(A);
+  } else {
+    k_adj_mid<<<grid, kAB, 0, s>>>(A);
+    k_adj_late<<<grid, kAB, 0, s>>>(A);
+    k_adj_finish<<<grid, kAB, 0, s>>>(A);
+  }
   return cudaGetLastError();
 }
 

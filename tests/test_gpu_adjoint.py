@@ -168,3 +168,24 @@ def test_legacy_stream_runs_without_graphs(pf):
     assert abs(out[0][0] - out[1][0]) <= 1e-12 * abs(out[0][0])
     assert abs(out[0][1] - out[1][1]) <= 1e-12 * abs(out[0][1])
     np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
+def test_adjoint_on_a_grid_above_the_fused_tail_limit(pf, orc):
+    """640 x 420 nodes (more than the 262 144 up to which the last three
+    reverse stages run as one tiled kernel): the separate-kernel path against
+    central differences of the FP64 oracle."""
+    import torch
+    nx, ny, wall, form = 640, 420, True, "CSF1"
+    phi0 = wl.drop(nx, ny, 60.0, 4.0, xc=301.7, yc=209.6, periodic_y=False).astype(np.float32)
+    target = wl.drop(nx, ny, 64.0, 4.0, periodic_y=False).astype(np.float32)
+    p = dict(sigma=0.02, W=4.0, M=0.1, rho1=1.0, rho2=0.5, nu1=0.1, nu2=0.05, gy=-1e-5,
+             uw_bottom=-0.01, uw_top=0.01, form=form)
+    p["rho0"] = float(np.mean(0.5 * (1 + phi0) + 0.25 * (1 - phi0)))
+    T, every = 8, 3
+    ds, dm, _, _ = _gpu_adjoint(pf, nx, ny, wall, p, phi0, target, T, every)
+    e = 1e-6
+    J = lambda **kw: _oracle_J(orc, nx, ny, wall, {**p, **kw}, phi0, target, T)
+    fd_s = (J(sigma=p["sigma"] * (1 + e)) - J(sigma=p["sigma"] * (1 - e))) / (2 * e * p["sigma"])
+    fd_m = (J(M=p["M"] * (1 + e)) - J(M=p["M"] * (1 - e))) / (2 * e * p["M"])
+    assert abs(ds - fd_s) <= 1e-4 * abs(fd_s) + 1e-7, (ds, fd_s)
+    assert abs(dm - fd_m) <= 1e-4 * abs(fd_m) + 1e-7, (dm, fd_m)
