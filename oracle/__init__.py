@@ -189,8 +189,15 @@ class Sim:
     """One oracle run: pre-collision populations f, h at the current time,
     (phi u) of the previous step, and the step counter."""
 
-    def __init__(self, nx: int, ny: int, wall_y: bool, par: Params, phi0: np.ndarray):
-        self.nx, self.ny, self.wall = int(nx), int(ny), bool(wall_y)
+    def __init__(self, nx: int, ny: int, wall_y: bool, par: Params, phi0: np.ndarray,
+                 wall_x: bool = False):
+        # boundary flags of the C oracle: bit 0 no-slip walls in y, bit 1
+        # free-slip (mirror-symmetry) walls in x
+        self.nx, self.ny = int(nx), int(ny)
+        self.wall = (1 if wall_y else 0) | (2 if wall_x else 0)
+        if wall_x and (par.gx != 0.0 or par.uw_bottom != 0.0 or par.uw_top != 0.0):
+            # x-odd forcing would break the mirror symmetry that defines the walls
+            raise ValueError("free-slip side walls need gx = 0 and walls at rest in y")
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(ny, nx)
         if math.isnan(par.rho0):
             par = Params(**{**par.__dict__, "rho0": mean_rho(par, phi0)})
@@ -298,13 +305,13 @@ def lib32():
     return _lib32
 
 
-def float32_deviation(nx, ny, wall_y, par: Params, phi0, steps: int) -> dict:
+def float32_deviation(nx, ny, wall_y, par: Params, phi0, steps: int, wall_x: bool = False) -> dict:
     """Max |phi| and |u| deviation after `steps` steps between the FP64 oracle
     and the same algorithm run with float32 state (pflbm_oracle_f32.c), both
     from phi0.  It measures the rounding sensitivity of a workload, from which
     tests derive the tolerance of a float32 implementation."""
-    a = Sim(nx, ny, wall_y, par, phi0)
-    b = Sim(nx, ny, wall_y, par, phi0)
+    a = Sim(nx, ny, wall_y, par, phi0, wall_x)
+    b = Sim(nx, ny, wall_y, par, phi0, wall_x)
     a.step(steps)
     L = lib32()
     L.w32_step(_p(b.pv), b.nx, b.ny, int(b.wall), _p(b.f), _p(b.h), _p(b.phiu_prev),

@@ -33,6 +33,8 @@
  *     phi u is phi (2 u_w - u) of the mirrored node.
  *   - d_t(phi u) is the backward difference over one step, zero at the first
  *     step of a run.
+ *   - Free-slip side walls (rising-bubble benchmark, Sec. 5.4): planes of
+ *     mirror symmetry at x = -1/2 and nx - 1/2 (see orc_step below).
  *
  * Layout: populations are [9][ny][nx] row-major (x fastest), fields [ny][nx].
  * Direction order c_0..c_8 = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),
@@ -264,7 +266,7 @@ static void force_sf(const Grid* g, const double* p, int form, const double* m,
 /* Macroscopic pass: every field of one time level from the pre-collision
  * populations f, h (post-streaming, time t) and (phi u)^{t-1}.
  * out: M_NFIELDS blocks of [ny][nx]. */
-void orc_macro(const double* p, int nx, int ny, int wall, const double* f,
+static void macro_px(const double* p, int nx, int ny, int wall, const double* f,
                const double* h, const double* phiu_prev, int first, double* out) {
   Grid g = {nx, ny, wall};
   size_t n = (size_t)nx * ny;
@@ -410,8 +412,8 @@ void orc_macro(const double* p, int nx, int ny, int wall, const double* f,
 /* Advance (f, h, phiu_prev) by nsteps steps in place.  f, h are the
  * pre-collision populations at time t; on return they are those at t+nsteps.
  * `first` marks that the first of these steps is the first of the run. */
-void orc_step(const double* p, int nx, int ny, int wall, double* f, double* h,
-              double* phiu_prev, int nsteps, int first) {
+static void step_px(const double* p, int nx, int ny, int wall, double* f, double* h,
+                    double* phiu_prev, int nsteps, int first) {
   Grid g = {nx, ny, wall};
   size_t n = (size_t)nx * ny;
   double* m = (double*)malloc(sizeof(double) * M_NFIELDS * n);
@@ -421,7 +423,7 @@ void orc_step(const double* p, int nx, int ny, int wall, double* f, double* h,
   double eta = p[P_M] / ((tau_h - 0.5) / 3.0); /* M = cs^2 eta (tau_h - 1/2) */
 
   for (int step = 0; step < nsteps; ++step) {
-    orc_macro(p, nx, ny, wall, f, h, phiu_prev, first && step == 0, m);
+    macro_px(p, nx, ny, wall, f, h, phiu_prev, first && step == 0, m);
 
     /* 7. collision */
 #pragma omp parallel for schedule(static)
@@ -483,8 +485,8 @@ void orc_step(const double* p, int nx, int ny, int wall, double* f, double* h,
 
 /* Initial state (phi0 given, u = 0, P = 0): f = f^eq(0, rho, 0) = 0 and
  * h = h^eq(phi0, mu0, 0) with mu0 from the chemical potential of phi0. */
-void orc_init(const double* p, int nx, int ny, int wall, const double* phi0,
-              double* f, double* h, double* phiu_prev) {
+static void init_px(const double* p, int nx, int ny, int wall, const double* phi0,
+                    double* f, double* h, double* phiu_prev) {
   Grid g = {nx, ny, wall};
   size_t n = (size_t)nx * ny;
   double beta = beta_of(p), kap = kappa_of(p);
@@ -508,7 +510,7 @@ void orc_init(const double* p, int nx, int ny, int wall, const double* phi0,
 
 /* Stand-alone central-scheme operators on a periodic or walled field, for
  * the stencil tests: out = [gx | gy | lap], each [ny][nx]. */
-void orc_ics(int nx, int ny, int wall, const double* a, double* out) {
+static void ics_px(int nx, int ny, int wall, const double* a, double* out) {
   Grid g = {nx, ny, wall};
   size_t n = (size_t)nx * ny;
   for (int y = 0; y < ny; ++y)
@@ -520,6 +522,128 @@ void orc_ics(int nx, int ny, int wall, const double* a, double* out) {
       out[n + k] = gy;
       out[2 * n + k] = ics_lap_node(&g, a, x, y);
     }
+}
+
+/* --------------------------------------------------------------------- */
+/* free-slip walls at x = -1/2 and x = nx - 1/2 (bit 1 of `wall`)          */
+/* --------------------------------------------------------------------- */
+/* A free-slip (specular) wall is a plane of mirror symmetry.  A domain with
+ * such walls at x = -1/2 and nx - 1/2 is therefore one half of the periodic
+ * domain of width 2 nx whose state is mirror-symmetric about x = nx - 1/2:
+ * node x of the other half is 2 nx - 1 - x, population i there is the mirror
+ * population (c_x reversed) of the node it mirrors, and x-odd fields (the x
+ * component of phi u) change sign.  The oracle is that definition written
+ * out: every step builds the symmetric doubled state from this half, runs one
+ * periodic-x step on it and keeps this half.  The doubled domain is symmetric
+ * only when the forcing is: gravity along x and wall motion along x (both odd
+ * under the mirror) must be zero, which the caller checks. */
+static const int mirx[NQ] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
+
+static void dbl_pops(int nx, int ny, const double* a, double* d) {
+  size_t n = (size_t)nx * ny, n2 = 2 * n;
+  for (int i = 0; i < NQ; ++i)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < 2 * nx; ++x)
+        d[i * n2 + (size_t)y * 2 * nx + x] =
+            x < nx ? a[i * n + (size_t)y * nx + x]
+                   : a[mirx[i] * n + (size_t)y * nx + (2 * nx - 1 - x)];
+}
+static void dbl_field(int nx, int ny, const double* a, double* d, double sign) {
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < 2 * nx; ++x)
+      d[(size_t)y * 2 * nx + x] =
+          x < nx ? a[(size_t)y * nx + x] : sign * a[(size_t)y * nx + (2 * nx - 1 - x)];
+}
+static void half_planes(int nx, int ny, int planes, const double* d, double* a) {
+  size_t n = (size_t)nx * ny, n2 = 2 * n;
+  for (int i = 0; i < planes; ++i)
+    for (int y = 0; y < ny; ++y)
+      memcpy(a + i * n + (size_t)y * nx, d + i * n2 + (size_t)y * 2 * nx, sizeof(double) * nx);
+}
+
+void orc_macro(const double* p, int nx, int ny, int wall, const double* f, const double* h,
+               const double* phiu_prev, int first, double* out) {
+  if (!(wall & 2)) {
+    macro_px(p, nx, ny, wall, f, h, phiu_prev, first, out);
+    return;
+  }
+  size_t n2 = (size_t)2 * nx * ny;
+  double* fd = (double*)malloc(sizeof(double) * NQ * n2);
+  double* hd = (double*)malloc(sizeof(double) * NQ * n2);
+  double* qd = (double*)malloc(sizeof(double) * 2 * n2);
+  double* od = (double*)malloc(sizeof(double) * M_NFIELDS * n2);
+  dbl_pops(nx, ny, f, fd);
+  dbl_pops(nx, ny, h, hd);
+  dbl_field(nx, ny, phiu_prev, qd, -1.0);
+  dbl_field(nx, ny, phiu_prev + (size_t)nx * ny, qd + n2, 1.0);
+  macro_px(p, 2 * nx, ny, wall & 1, fd, hd, qd, first, od);
+  half_planes(nx, ny, M_NFIELDS, od, out);
+  free(fd);
+  free(hd);
+  free(qd);
+  free(od);
+}
+
+void orc_step(const double* p, int nx, int ny, int wall, double* f, double* h,
+              double* phiu_prev, int nsteps, int first) {
+  if (!(wall & 2)) {
+    step_px(p, nx, ny, wall, f, h, phiu_prev, nsteps, first);
+    return;
+  }
+  size_t n = (size_t)nx * ny, n2 = 2 * n;
+  double* fd = (double*)malloc(sizeof(double) * NQ * n2);
+  double* hd = (double*)malloc(sizeof(double) * NQ * n2);
+  double* qd = (double*)malloc(sizeof(double) * 2 * n2);
+  for (int s = 0; s < nsteps; ++s) {
+    dbl_pops(nx, ny, f, fd);
+    dbl_pops(nx, ny, h, hd);
+    dbl_field(nx, ny, phiu_prev, qd, -1.0);
+    dbl_field(nx, ny, phiu_prev + n, qd + n2, 1.0);
+    step_px(p, 2 * nx, ny, wall & 1, fd, hd, qd, 1, first && s == 0);
+    half_planes(nx, ny, NQ, fd, f);
+    half_planes(nx, ny, NQ, hd, h);
+    half_planes(nx, ny, 2, qd, phiu_prev);
+  }
+  free(fd);
+  free(hd);
+  free(qd);
+}
+
+void orc_init(const double* p, int nx, int ny, int wall, const double* phi0, double* f,
+              double* h, double* phiu_prev) {
+  if (!(wall & 2)) {
+    init_px(p, nx, ny, wall, phi0, f, h, phiu_prev);
+    return;
+  }
+  size_t n2 = (size_t)2 * nx * ny;
+  double* pd = (double*)malloc(sizeof(double) * n2);
+  double* fd = (double*)malloc(sizeof(double) * NQ * n2);
+  double* hd = (double*)malloc(sizeof(double) * NQ * n2);
+  double* qd = (double*)malloc(sizeof(double) * 2 * n2);
+  dbl_field(nx, ny, phi0, pd, 1.0);
+  init_px(p, 2 * nx, ny, wall & 1, pd, fd, hd, qd);
+  half_planes(nx, ny, NQ, fd, f);
+  half_planes(nx, ny, NQ, hd, h);
+  half_planes(nx, ny, 2, qd, phiu_prev);
+  free(pd);
+  free(fd);
+  free(hd);
+  free(qd);
+}
+
+void orc_ics(int nx, int ny, int wall, const double* a, double* out) {
+  if (!(wall & 2)) {
+    ics_px(nx, ny, wall, a, out);
+    return;
+  }
+  size_t n2 = (size_t)2 * nx * ny;
+  double* ad = (double*)malloc(sizeof(double) * n2);
+  double* od = (double*)malloc(sizeof(double) * 3 * n2);
+  dbl_field(nx, ny, a, ad, 1.0);
+  ics_px(2 * nx, ny, wall & 1, ad, od);
+  half_planes(nx, ny, 3, od, out);
+  free(ad);
+  free(od);
 }
 
 int orc_nfields(void) { return M_NFIELDS; }
