@@ -53,7 +53,14 @@ typedef enum {
   PFLBM_ESTATE = 6      /* call out of order (no params / no initial phi) */
 } pflbm_status;
 
-typedef enum { PFLBM_PERIODIC = 0, PFLBM_WALL = 1 } pflbm_bc;
+/* Boundaries: PERIODIC; WALL (y only): half-way bounce-back no-slip walls,
+ * moving along x at uw_bottom / uw_top (Sec. 4); FREESLIP (x only):
+ * free-slip side walls at x = -1/2 and nx - 1/2, planes of mirror symmetry
+ * (specular reflection of the populations, mirror ghosts for the stencils),
+ * as in the rising-bubble benchmark (Sec. 5.4).  Free-slip side walls need
+ * gx = 0 and y-walls at rest, run the gather staging only, and are not
+ * supported by batches or the adjoint. */
+typedef enum { PFLBM_PERIODIC = 0, PFLBM_WALL = 1, PFLBM_FREESLIP = 2 } pflbm_bc;
 
 /* Interfacial force formulations (Sec. 2.2):
  *   STF1  -div(kappa grad phi (x) grad phi)                    Eq. SF1
@@ -139,7 +146,8 @@ size_t pflbm_workspace_bytes(int nx, int ny, pflbm_storage storage);
 
 /* Create a domain over a caller-owned device workspace (256-byte aligned,
  * at least pflbm_workspace_bytes) and CUDA stream (cudaStream_t, NULL = the
- * legacy default stream).  bc_x must be PFLBM_PERIODIC; bc_y may be either.
+ * legacy default stream).  bc_x is PFLBM_PERIODIC or PFLBM_FREESLIP; bc_y is
+ * PFLBM_PERIODIC or PFLBM_WALL.
  * nx, ny >= 4.  The domain (Sec. 5 benchmarks) is the paper's uniform
  * L_x x L_y lattice.  Errors: EINVAL, ENOMEM_WS. */
 pflbm_status pflbm_create(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y,

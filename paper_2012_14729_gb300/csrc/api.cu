@@ -71,6 +71,7 @@ void pflbm::set_last_error(const char* msg) { set_msg(msg); }
 
 struct pflbm_domain {
   int nx, ny, wall, storage;
+  int wall_x;  // free-slip side walls
   cudaStream_t stream;
   char* ws;
   Layout lay;
@@ -104,6 +105,7 @@ StepArgs make_args(const pflbm_domain* d, int from) {
   a.L.nx = d->nx;
   a.L.ny = d->ny;
   a.L.wall = d->wall;
+  a.L.wall_x = d->wall_x;
   a.L.plane = (d->ny + 2) * d->nx;
   a.p = d->phys;
   const int to = 1 - from;
@@ -290,7 +292,8 @@ pflbm_status pflbm_create(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y, pflbm_st
   if (!out) return PFLBM_EINVAL;
   *out = nullptr;
   Layout L;
-  if (bc_x != PFLBM_PERIODIC || (bc_y != PFLBM_PERIODIC && bc_y != PFLBM_WALL) ||
+  if ((bc_x != PFLBM_PERIODIC && bc_x != PFLBM_FREESLIP) ||
+      (bc_y != PFLBM_PERIODIC && bc_y != PFLBM_WALL) ||
       !layout_of(nx, ny, (int)storage, &L) || !dev_workspace ||
       ((uintptr_t)dev_workspace % kAlign) != 0) {
     set_msg("pflbm_create: invalid argument");
@@ -306,6 +309,7 @@ pflbm_status pflbm_create(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y, pflbm_st
   d->nx = nx;
   d->ny = ny;
   d->wall = bc_y == PFLBM_WALL;
+  d->wall_x = bc_x == PFLBM_FREESLIP;
   d->storage = (int)storage;
   d->stream = (cudaStream_t)cuda_stream;
   d->ws = (char*)dev_workspace;
@@ -325,6 +329,10 @@ pflbm_status pflbm_set_params(pflbm_domain* d, const pflbm_params* p) {
                   (p->scale_h == 0 || is_pow2(p->scale_h));
   if (!ok) {
     set_msg("pflbm_set_params: parameter out of range");
+    return PFLBM_EINVAL;
+  }
+  if (d->wall_x && (p->gx != 0 || p->uw_bottom != 0 || p->uw_top != 0)) {
+    set_msg("pflbm_set_params: free-slip side walls need gx = 0 and walls at rest in y");
     return PFLBM_EINVAL;
   }
   d->par = *p;
@@ -416,6 +424,10 @@ pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
 
 pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode) {
   if (!d || mode < 0 || mode >= kNumModes) return PFLBM_EINVAL;
+  if (d->wall_x && mode != kGather) {
+    set_msg("pflbm_set_stage_mode: side walls are staged by gathers only");
+    return PFLBM_EINVAL;
+  }
   d->mode = mode;
   drop_graph(d);
   return PFLBM_OK;
@@ -441,6 +453,7 @@ pflbm_status pflbm_autotune(pflbm_domain* d, int trial_steps, int* mode_out) {
   float best = 1e30f;
   int best_mode = d->mode;
   for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
+    if (d->wall_x && m != kGather) continue;  // side walls: gathers only
     e = launch_step_mode(d, m, a);  // warm-up (also sets kernel attributes)
     if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
     for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_step_mode(d, m, a);
@@ -623,7 +636,7 @@ pflbm_status pflbm_save_state(pflbm_domain* d, void* dst, int on_device) {
   if (!d || !dst) return PFLBM_EINVAL;
   if (!d->has_state) return PFLBM_ESTATE;
   const Layout& L = d->lay;
-  long long hdr[8] = {0x70666c626d, d->t, d->nx, d->ny, d->storage, d->wall, 0, 0};
+  long long hdr[8] = {0x70666c626d, d->t, d->nx, d->ny, d->storage, d->wall, d->wall_x, 0};
   char* p = (char*)dst;
   const cudaMemcpyKind h2x = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
   const cudaMemcpyKind d2x = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -660,7 +673,7 @@ pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device) {
     return PFLBM_ECUDA;
   }
   if (hdr[0] != 0x70666c626d || hdr[2] != d->nx || hdr[3] != d->ny || hdr[4] != d->storage ||
-      hdr[5] != d->wall) {
+      hdr[5] != d->wall || hdr[6] != d->wall_x) {
     set_msg("pflbm_load_state: state does not match this domain");
     return PFLBM_EINVAL;
   }
@@ -713,7 +726,7 @@ struct AdjLayout {
 };
 
 bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
-  if (!d || nsteps < 1 || every < 1 || d->storage != kFP32) return false;
+  if (!d || nsteps < 1 || every < 1 || d->storage != kFP32 || d->wall_x) return false;
   const size_t n = (size_t)d->nx * d->ny;
   L->blob = align_up(pflbm_state_bytes(d));
   L->ncp = (nsteps + every - 1) / every;
@@ -793,7 +806,8 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
   AdjLayout L;
   if (!d || !phi0 || !dJ_dphiT || !dJ_dphi0 || !scratch ||
       !adj_layout(d, nsteps, ckpt_every, &L)) {
-    set_msg("pflbm_adjoint_run: invalid argument (FP32 storage, nsteps, ckpt_every >= 1)");
+    set_msg("pflbm_adjoint_run: invalid argument (FP32 storage, periodic x, nsteps, "
+            "ckpt_every >= 1)");
     return PFLBM_EINVAL;
   }
   if (!d->has_params) return PFLBM_ESTATE;
@@ -987,8 +1001,9 @@ pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_work
     return PFLBM_EINVAL;
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
-    if (!doms[i] || doms[i]->storage != kFP32) {
-      set_msg("pflbm_batch_create: every domain must exist and use FP32 storage");
+    if (!doms[i] || doms[i]->storage != kFP32 || doms[i]->wall_x) {
+      set_msg("pflbm_batch_create: every domain must exist, use FP32 storage and be "
+              "periodic in x");
       return PFLBM_EINVAL;
     }
     if (!doms[i]->has_state) {

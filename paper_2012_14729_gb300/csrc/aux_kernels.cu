@@ -21,8 +21,29 @@ int num_sms() {
 // initial state (zero velocity, Sec. 5.1): f = f^eq(P = 0, u = 0) = 0 and
 // h = h^eq(phi0, mu0, 0) with mu0 = 4 beta phi0 (phi0^2 - 1) - kappa lap phi0.
 // The pre-collision value h_i(x) is written where the first pull reads it:
-// population plane i at x - c_i (ghost rows for walls, wrapped otherwise).
+// population plane i at x - c_i (ghost rows for walls, wrapped otherwise;
+// beyond a free-slip side wall, plane M, the mirror direction, in x's own
+// column, where the specular pull reads).
 // ---------------------------------------------------------------------------
+template <class ST, int I, int M>
+__device__ __forceinline__ void put_h(const StepArgs& a, int x, int y, float v) {
+  const Lattice& L = a.L;
+  int sx = x - qcx(I), sy = y - qcy(I);
+  if (!L.wall) {
+    if (sy < 0) sy += L.ny;
+    if (sy >= L.ny) sy -= L.ny;
+  }
+  const int row = (sy + 1) * L.nx;
+  if (sx < 0 || sx >= L.nx) {
+    if (L.wall_x) {
+      store_h<ST, M>(a, row + x, v);
+      return;
+    }
+    sx = sx < 0 ? sx + L.nx : sx - L.nx;
+  }
+  store_h<ST, I>(a, row + sx, v);
+}
+
 template <class ST>
 __global__ void k_init(const StepArgs a, const float* __restrict__ phi0) {
   const Lattice L = a.L;
@@ -30,7 +51,7 @@ __global__ void k_init(const StepArgs a, const float* __restrict__ phi0) {
   const int y = blockIdx.y;
   if (x >= L.nx || y >= L.ny) return;
   auto at = [&](int dx, int dy) {
-    return phi0[map_row(y + dy, L.ny, L.wall) * L.nx + wrap(x + dx, L.nx)];
+    return phi0[map_row(y + dy, L.ny, L.wall) * L.nx + map_col(x + dx, L.nx, L.wall_x)];
   };
   const float pc = at(0, 0);
   const float lap = ((at(1, 0) - pc) + (at(-1, 0) - pc) + (at(0, 1) - pc) + (at(0, -1) - pc)) *
@@ -39,27 +60,15 @@ __global__ void k_init(const StepArgs a, const float* __restrict__ phi0) {
                         (1.0f / 6.0f);
   const float mu = a.p.beta4 * pc * ((pc - 1.0f) * (pc + 1.0f)) - a.p.kappa * lap;
   const float emu = a.p.eta * mu;
-  // destination of population i: storage position of x - c_i
-  auto dst = [&](int cxi, int cyi) {
-    int sx = x - cxi;
-    if (sx < 0) sx += L.nx;
-    if (sx >= L.nx) sx -= L.nx;
-    int sy = y - cyi;
-    if (!L.wall) {
-      if (sy < 0) sy += L.ny;
-      if (sy >= L.ny) sy -= L.ny;
-    }
-    return (sy + 1) * L.nx + sx;
-  };
-  store_h<ST, 0>(a, dst(0, 0), pc + (qw(0) - 1.0f) * emu);
-  store_h<ST, 1>(a, dst(1, 0), qw(1) * emu);
-  store_h<ST, 2>(a, dst(0, 1), qw(2) * emu);
-  store_h<ST, 3>(a, dst(-1, 0), qw(3) * emu);
-  store_h<ST, 4>(a, dst(0, -1), qw(4) * emu);
-  store_h<ST, 5>(a, dst(1, 1), qw(5) * emu);
-  store_h<ST, 6>(a, dst(-1, 1), qw(6) * emu);
-  store_h<ST, 7>(a, dst(-1, -1), qw(7) * emu);
-  store_h<ST, 8>(a, dst(1, -1), qw(8) * emu);
+  put_h<ST, 0, 0>(a, x, y, pc + (qw(0) - 1.0f) * emu);
+  put_h<ST, 1, 3>(a, x, y, qw(1) * emu);
+  put_h<ST, 2, 2>(a, x, y, qw(2) * emu);
+  put_h<ST, 3, 1>(a, x, y, qw(3) * emu);
+  put_h<ST, 4, 4>(a, x, y, qw(4) * emu);
+  put_h<ST, 5, 6>(a, x, y, qw(5) * emu);
+  put_h<ST, 6, 5>(a, x, y, qw(6) * emu);
+  put_h<ST, 7, 8>(a, x, y, qw(7) * emu);
+  put_h<ST, 8, 7>(a, x, y, qw(8) * emu);
   const int n = L.nx * L.ny;
   a.phiu[y * L.nx + x] = 0.0f;
   a.phiu[n + y * L.nx + x] = 0.0f;
@@ -85,7 +94,7 @@ __global__ void k_read_pops(const StepArgs a, float* f_out, float* h_out) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= L.nx || y >= L.ny) return;
-  const Pull q = pull_idx(L, x, y);
+  const Pull q = L.wall_x ? pull_idx<true>(L, x, y) : pull_idx<false>(L, x, y);
   const int n = L.nx * L.ny, o = y * L.nx + x;
   float v[9];
   if (f_out) {
@@ -163,7 +172,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
     acc[7] += w * x * y;
     if (g.has_geom) {
       double dx = fabs(x - g.xc), dy = fabs(y - g.yc);
-      dx = fmin(dx, L.nx - dx);
+      if (!L.wall_x) dx = fmin(dx, L.nx - dx);  // periodic distance across x
       dy = fmin(dy, L.ny - dy);
       const double r = sqrt(dx * dx + dy * dy);
       if (r <= g.r_in) {

@@ -40,6 +40,7 @@ struct Lattice {
   int nx, ny;
   int wall;          // 1: half-way bounce-back walls at y = -1/2, ny - 1/2
   int plane;         // elements per population plane: (ny + 2) * nx
+  int wall_x;        // 1: free-slip (mirror-symmetry) walls at x = -1/2, nx - 1/2
 };
 
 // Arguments of one fused step (or macroscopic read) over one domain.  The

@@ -127,32 +127,54 @@ __device__ __forceinline__ int map_row(int y, int ny, int wall) {
   return y;
 }
 
+// Column of a scalar-field node: periodic wrap, or mirror about free-slip
+// side walls (ghost column -k = column k - 1).
+__device__ __forceinline__ int map_col(int x, int nx, int wall_x) {
+  if (x >= 0 && x < nx) return x;
+  if (!wall_x) return wrap(x, nx);
+  while (x < 0 || x >= nx) x = (x < 0) ? -x - 1 : 2 * nx - 1 - x;
+  return x;
+}
+
 // Storage indices of the 9 pulled populations of node (x, y), 0 <= x < nx,
 // 0 <= y < ny: population i comes from (x - cx_i, y - cy_i); storage row is
-// domain row + 1 (ghost rows 0 and ny + 1 hold bounced populations).
+// domain row + 1 (ghost rows 0 and ny + 1 hold bounced populations).  At a
+// free-slip side wall a population whose source lies beyond the wall is the
+// specular reflection of the population leaving the node's own column in the
+// mirror direction (cx reversed): the index then points into that
+// population's plane (planes are `plane` elements apart).
 struct Pull {
   int i[9];
 };
+template <bool XW = false>
 __device__ __forceinline__ Pull pull_idx(const Lattice& L, int x, int y) {
   int xm = x + 1, xp = x - 1;  // source columns for cx = -1 and cx = +1
-  if (xm >= L.nx) xm -= L.nx;
-  if (xp < 0) xp += L.nx;
+  int dm = 0, dp = 0;          // plane offset (in planes) of the mirror direction
+  if (xm >= L.nx) {
+    if (XW) xm = x, dm = 1;  // 3 <- 1, 6 <- 5, 7 <- 8
+    else xm -= L.nx;
+  }
+  if (xp < 0) {
+    if (XW) xp = x, dp = 1;  // 1 <- 3, 5 <- 6, 8 <- 7
+    else xp += L.nx;
+  }
   int ym = y + 1, yp = y - 1;  // source rows for cy = -1 and cy = +1
   if (!L.wall) {
     if (ym >= L.ny) ym -= L.ny;
     if (yp < 0) yp += L.ny;
   }
   const int r0 = (y + 1) * L.nx, rm = (ym + 1) * L.nx, rp = (yp + 1) * L.nx;
+  const int pl = L.plane;
   Pull p;
   p.i[0] = r0 + x;
-  p.i[1] = r0 + xp;
+  p.i[1] = r0 + xp + dp * 2 * pl;
   p.i[2] = rp + x;
-  p.i[3] = r0 + xm;
+  p.i[3] = r0 + xm - dm * 2 * pl;
   p.i[4] = rm + x;
-  p.i[5] = rp + xp;
-  p.i[6] = rp + xm;
-  p.i[7] = rm + xm;
-  p.i[8] = rm + xp;
+  p.i[5] = rp + xp + dp * pl;
+  p.i[6] = rp + xm - dm * pl;
+  p.i[7] = rm + xm + dm * pl;
+  p.i[8] = rm + xp - dp * pl;
   return p;
 }
 

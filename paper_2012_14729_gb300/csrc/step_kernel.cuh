@@ -139,7 +139,7 @@ struct Boxes {
 // pulled at a node sits at box column (node column - c_ix) of its row.
 template <class ST>
 struct BoxSrc {
-  static constexpr bool kInner = false;
+  static constexpr bool kInner = false, kWallX = false;
   using G = Boxes<ST>;
   const unsigned char* bx;
   template <int I>
@@ -218,12 +218,13 @@ struct BoxSrc {
 // Straight from the population planes (global coordinates of the node).
 // INNER: the tile and its 3-ring pull only from inside the domain, so node
 // coordinates need no wrap or mirror and pulls no ghost row.
-template <class ST, bool INNER = false>
+// XW: free-slip side walls (specular pulls at x = 0 and nx - 1).
+template <class ST, bool INNER = false, bool XW = false>
 struct GatherSrc {
-  static constexpr bool kInner = INNER;
+  static constexpr bool kInner = INNER, kWallX = XW;
   __device__ __forceinline__ static Pull idx(const Lattice& L, int gx, int gy) {
     if constexpr (INNER) return pull_idx_inner(L, gx, gy);
-    else return pull_idx(L, gx, gy);
+    else return pull_idx<XW>(L, gx, gy);
   }
   __device__ __forceinline__ float phi(const StepArgs& a, int, int, int gx, int gy) const {
     return pull_phi<ST>(a, idx(a.L, gx, gy));
@@ -426,6 +427,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   const int tid = threadIdx.x;
   const int nn = L.nx * L.ny;
   constexpr bool kIn = SRC::kInner;
+  constexpr bool kXw = SRC::kWallX;  // free-slip side walls (mirror columns)
+  const auto col = [&](int x) { return kXw ? map_col(x, L.nx, 1) : wrap(x, L.nx); };
 
   // (phi u)^{t-1} of this thread's collision nodes, loaded first so that the
   // load latency overlaps passes 1-3
@@ -449,7 +452,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const int yn = y0 - 3 + r;
     if (!kIn && L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
     sPhi[k] = kIn ? src.phi(a, r, cc, x0 - 3 + cc, yn)
-                  : src.phi(a, r, cc, wrap(x0 - 3 + cc, L.nx), L.wall ? yn : wrap(yn, L.ny));
+                  : src.phi(a, r, cc, col(x0 - 3 + cc), L.wall ? yn : wrap(yn, L.ny));
   }
   __syncthreads();
   if (!kIn && L.wall && (y0 - 3 < 0 || y0 + kTY + 3 > L.ny)) {
@@ -473,7 +476,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   if constexpr (kPre) {
     const int ly = tid / B1X, lx = tid - ly * B1X;
     if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, fpre);
-    else src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), fpre);
+    else src.f_ring1(a, ly, lx, col(x0 - 1 + lx), map_row(y0 - 1 + ly, L.ny, L.wall), fpre);
   }
 
   // ---- pass 2: grad phi, lap phi, mu, level-1 fields on tile + 2 -------------
@@ -585,7 +588,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   auto load_ring1 = [&](int k, float* f) {
     const int ly = k / B1X, lx = k - ly * B1X;
     if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, f);
-    else src.f_ring1(a, ly, lx, wrap(x0 - 1 + lx, L.nx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
+    else src.f_ring1(a, ly, lx, col(x0 - 1 + lx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
   };
   if constexpr (kPre) pass3(tid, fpre);
   for (int k = kPre ? tid + NT : tid; k < N1; k += NT) {
@@ -614,6 +617,29 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
           const float pm = sPhi[(lt - 1 + 2) * B3X + lx + 2];
           s1[PUX * N1 + g] = pm * (2.0f * P.uwt - s1[UX * N1 + m]);
           s1[PUY * N1 + g] = -pm * s1[UY * N1 + m];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // free-slip side walls: the ghost column of phi u is (-phi u_x, phi u_y) of
+  // the mirrored column (after the y ghosts, so that the corners mirror them)
+  if constexpr (kXw) {
+    const int cl = -x0;             // ring-1 column of x = -1
+    const int cr = L.nx - (x0 - 1);  // ring-1 column of x = nx
+    const bool left = cl >= 0 && cl + 1 < B1X;
+    const bool right = cr - 1 >= 0 && cr < B1X;
+    if (left || right) {
+      for (int ly = tid; ly < B1Y; ly += NT) {
+        if (left) {
+          const int g = ly * B1X + cl;
+          s1[PUX * N1 + g] = -s1[PUX * N1 + g + 1];
+          s1[PUY * N1 + g] = s1[PUY * N1 + g + 1];
+        }
+        if (right) {
+          const int g = ly * B1X + cr;
+          s1[PUX * N1 + g] = -s1[PUX * N1 + g - 1];
+          s1[PUY * N1 + g] = s1[PUY * N1 + g - 1];
         }
       }
     }
@@ -768,16 +794,33 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       // next pull reads it from.
       const int xr = gx + 1 < L.nx ? gx + 1 : 0;        // x + 1
       const int xl = gx - 1 >= 0 ? gx - 1 : L.nx - 1;   // x - 1
+      // beyond a free-slip side wall the ghost-row slot of x -+ 1 is the
+      // mirror direction's slot in this column (where the specular pull reads)
+      const bool lw = kXw && gx == 0, rw = kXw && gx == L.nx - 1;
       if (gy == 0) {
         const float uw = P.uwb;
         // i = 4 (0,-1) -> opp 2 at (x, -1); i = 7 (-1,-1) -> opp 5 at (x-1, -1);
         // i = 8 (1,-1) -> opp 6 at (x+1, -1)
         store_f<ST, 2>(a, gx, fo[4]);
         store_h<ST, 2>(a, gx, ho[4]);
-        store_f<ST, 5>(a, xl, fo[7] - 2.0f * qw(7) * rho * (-uw));
-        store_h<ST, 5>(a, xl, ho[7] - 2.0f * qw(7) * phi * 3.0f * (-uw));
-        store_f<ST, 6>(a, xr, fo[8] - 2.0f * qw(8) * rho * uw);
-        store_h<ST, 6>(a, xr, ho[8] - 2.0f * qw(8) * phi * 3.0f * uw);
+        const float f5 = fo[7] - 2.0f * qw(7) * rho * (-uw);
+        const float h5 = ho[7] - 2.0f * qw(7) * phi * 3.0f * (-uw);
+        if (lw) {
+          store_f<ST, 6>(a, gx, f5);
+          store_h<ST, 6>(a, gx, h5);
+        } else {
+          store_f<ST, 5>(a, xl, f5);
+          store_h<ST, 5>(a, xl, h5);
+        }
+        const float f6 = fo[8] - 2.0f * qw(8) * rho * uw;
+        const float h6 = ho[8] - 2.0f * qw(8) * phi * 3.0f * uw;
+        if (rw) {
+          store_f<ST, 5>(a, gx, f6);
+          store_h<ST, 5>(a, gx, h6);
+        } else {
+          store_f<ST, 6>(a, xr, f6);
+          store_h<ST, 6>(a, xr, h6);
+        }
       }
       if (gy == L.ny - 1) {
         const float uw = P.uwt;
@@ -786,10 +829,24 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
         // i = 6 (-1,1) -> opp 8 at (x-1, ny)
         store_f<ST, 4>(a, g + gx, fo[2]);
         store_h<ST, 4>(a, g + gx, ho[2]);
-        store_f<ST, 7>(a, g + xr, fo[5] - 2.0f * qw(5) * rho * uw);
-        store_h<ST, 7>(a, g + xr, ho[5] - 2.0f * qw(5) * phi * 3.0f * uw);
-        store_f<ST, 8>(a, g + xl, fo[6] - 2.0f * qw(6) * rho * (-uw));
-        store_h<ST, 8>(a, g + xl, ho[6] - 2.0f * qw(6) * phi * 3.0f * (-uw));
+        const float f7 = fo[5] - 2.0f * qw(5) * rho * uw;
+        const float h7 = ho[5] - 2.0f * qw(5) * phi * 3.0f * uw;
+        if (rw) {
+          store_f<ST, 8>(a, g + gx, f7);
+          store_h<ST, 8>(a, g + gx, h7);
+        } else {
+          store_f<ST, 7>(a, g + xr, f7);
+          store_h<ST, 7>(a, g + xr, h7);
+        }
+        const float f8 = fo[6] - 2.0f * qw(6) * rho * (-uw);
+        const float h8 = ho[6] - 2.0f * qw(6) * phi * 3.0f * (-uw);
+        if (lw) {
+          store_f<ST, 7>(a, g + gx, f8);
+          store_h<ST, 7>(a, g + gx, h8);
+        } else {
+          store_f<ST, 8>(a, g + xl, f8);
+          store_h<ST, 8>(a, g + xl, h8);
+        }
       }
     }
   }
@@ -839,8 +896,9 @@ __global__ void __launch_bounds__(kThreadsBoxes, kBlocksBoxes)
   }
 }
 
-// kGather: one CTA per tile, populations gathered through L1.
-template <int FORM, class ST>
+// kGather: one CTA per tile, populations gathered through L1.  XW: free-slip
+// side walls (a separate instantiation, so periodic domains run unchanged code).
+template <int FORM, class ST, bool XW>
 __global__ void __launch_bounds__(kThreadsGather, kBlocksGather)
     k_step_gather(const __grid_constant__ StepArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -849,7 +907,7 @@ __global__ void __launch_bounds__(kThreadsGather, kBlocksGather)
   if (inner_tile(a.L, x0, y0))
     step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, true>{}, sm, x0, y0);
   else
-    step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, false>{}, sm, x0, y0);
+    step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, false, XW>{}, sm, x0, y0);
 }
 
 // Taping step of the adjoint's recomputation (float32 storage, gathers): the
@@ -879,7 +937,10 @@ cudaError_t launch_form(int mode, const StepArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_step_boxes<FORM, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxBytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step_gather<FORM, ST>,
+      e = cudaFuncSetAttribute(k_step_gather<FORM, ST, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, kGatherBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step_gather<FORM, ST, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, kGatherBytes);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -889,7 +950,10 @@ cudaError_t launch_form(int mode, const StepArgs& a, cudaStream_t s) {
     const int slots = num_sms() * kBlocksBoxes;
     k_step_boxes<FORM, ST><<<ntiles < slots ? ntiles : slots, kThreadsBoxes, kBoxBytes, s>>>(a);
   } else {
-    k_step_gather<FORM, ST><<<ntiles, kThreadsGather, kGatherBytes, s>>>(a);
+    if (a.L.wall_x)
+      k_step_gather<FORM, ST, true><<<ntiles, kThreadsGather, kGatherBytes, s>>>(a);
+    else
+      k_step_gather<FORM, ST, false><<<ntiles, kThreadsGather, kGatherBytes, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -25,7 +25,7 @@ FAMILY = {"STF": "STF1", "CPF": "CPF1", "PF": "PF1", "CSF": "CSF1"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 FIELDS = ("phi", "rho", "ux", "uy", "P", "mu", "p_h", "Fx", "Fy")
 NOALLOC_MAX_NODES = 8388608  # PFLBM_NOALLOC_MAX_NODES
-PERIODIC, WALL = 0, 1
+PERIODIC, WALL, FREESLIP = 0, 1, 2
 
 STATUS = {0: "PFLBM_OK", 1: "PFLBM_EINVAL", 2: "PFLBM_ENOMEM_WS", 3: "PFLBM_ECUDA",
           4: "PFLBM_EUNSTABLE", 5: "PFLBM_ETIMEOUT", 6: "PFLBM_ESTATE"}
@@ -379,10 +379,11 @@ class Domain:
     uint8 tensor; the stream is a torch stream (a new one by default)."""
 
     def __init__(self, nx: int, ny: int, wall_y: bool = False, storage: str = "fp32",
-                 stream=None, device=None):
+                 stream=None, device=None, wall_x: bool = False):
         import torch
         self.torch = torch
         self.nx, self.ny, self.wall = int(nx), int(ny), bool(wall_y)
+        self.wall_x = bool(wall_x)  # free-slip side walls
         self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         self.device = torch.device(device or "cuda")
         nbytes = pflbm_workspace_bytes(nx, ny, self.storage)
@@ -390,7 +391,8 @@ class Domain:
             raise PflbmError(1, "pflbm_workspace_bytes", f"invalid size {nx}x{ny}")
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        self.h = pflbm_create(nx, ny, PERIODIC, WALL if wall_y else PERIODIC, self.storage,
+        self.h = pflbm_create(nx, ny, FREESLIP if wall_x else PERIODIC,
+                              WALL if wall_y else PERIODIC, self.storage,
                               self.ws.data_ptr(), nbytes, self.stream.cuda_stream)
 
     def __del__(self):
