@@ -8,7 +8,8 @@ The arithmetic lives in ``pflbm_oracle.c`` (plain loops, double precision,
 whole-grid passes in the order of the scheme); this module compiles it with
 gcc, calls it through ctypes, and adds the FP64 diagnostics of Sec. 5
 (Laplace pressure jump, spurious currents, mass, mass centre, Taylor
-deformation), written with numpy.
+deformation, the rising-bubble centre of mass, velocity and circularity with
+a marching-squares perimeter), written with numpy and plain loops.
 
 Parity of every function here is pinned by ``tests/test_oracle_*.py``
 against moment identities, closed forms, invariants and physical laws.
@@ -284,6 +285,90 @@ def taylor_D(fields: dict) -> float:
     l1, l2 = tr / 2 + disc, tr / 2 - disc
     L, B = 4 * math.sqrt(l1), 4 * math.sqrt(max(l2, 0.0))
     return (L - B) / (L + B)
+
+
+def _crossing(p, vp, q, vq):
+    """Point where the linear interpolant of phi between lattice points p and
+    q (values vp, vq of opposite side of zero) vanishes."""
+    t = vp / (vp - vq)
+    return (p[0] + t * (q[0] - p[0]), p[1] + t * (q[1] - p[1]))
+
+
+def _seg(a, b):
+    return math.hypot(a[0] - b[0], a[1] - b[1])
+
+
+def cell_contour_length(v) -> float:
+    """Length of the phi = 0 contour inside one lattice cell by marching
+    squares: v = (phi at (0,0), (1,0), (1,1), (0,1)), a corner is inside the
+    bubble when phi < 0, the contour crosses each edge whose ends differ at
+    the zero of the linear interpolant.  A cell with four crossings (inside
+    corners on one diagonal) is resolved by the mean of its four values: if
+    it is inside, the inside corners connect through the cell and each
+    segment cuts off an outside corner; otherwise each cuts off an inside
+    corner."""
+    P = ((0.0, 0.0), (1.0, 0.0), (1.0, 1.0), (0.0, 1.0))
+    ins = [x < 0 for x in v]
+    pts = {}  # edge k joins corner k and corner k+1
+    for k in range(4):
+        j = (k + 1) % 4
+        if ins[k] != ins[j]:
+            pts[k] = _crossing(P[k], v[k], P[j], v[j])
+    if len(pts) == 0:
+        return 0.0
+    if len(pts) == 2:
+        a, b = pts.values()
+        return _seg(a, b)
+    centre_in = (v[0] + v[1] + v[2] + v[3]) / 4.0 < 0
+    total = 0.0
+    for k in range(4):
+        if ins[k] != centre_in:  # the corner each segment cuts off
+            total += _seg(pts[(k - 1) % 4], pts[k])
+    return total
+
+
+def contour_length(phi: np.ndarray, wrap_x: bool, wrap_y: bool) -> float:
+    """Perimeter P_b of the bubble (Eq. circularity): the phi = 0 contour
+    over the cells of the node lattice (spacing 1), a cell per node with the
+    node as its lower-left corner; a periodic direction adds the cells that
+    wrap around, a wall direction has none beyond the last node."""
+    ny, nx = phi.shape
+    cx = nx if wrap_x else nx - 1
+    cy = ny if wrap_y else ny - 1
+    total = 0.0
+    for y in range(cy):
+        y1 = (y + 1) % ny
+        for x in range(cx):
+            x1 = (x + 1) % nx
+            v = (phi[y, x], phi[y, x1], phi[y1, x1], phi[y1, x])
+            if min(v) < 0 <= max(v):
+                total += cell_contour_length(v)
+    return total
+
+
+def rising_bubble(fields: dict, wall_x: bool, wall_y: bool) -> dict:
+    """Benchmark quantities of the rising bubble (Sec. 5.4), lattice units:
+    centre of mass (xc2, yc2) and velocity (uc2, vc2) of fluid 2 weighted by
+    1 - phi (Eqs. quantify-yc, quantify-uc, node coordinates x, y), the area
+    area2 = number of nodes with phi < 0, the perimeter of the phi = 0
+    contour and the circularity 2 sqrt(pi area2) / perimeter (Eq.
+    circularity; 0 when there is no contour; the means are 0 when no node
+    holds fluid 2)."""
+    phi = fields["phi"]
+    ny, nx = phi.shape
+    w = 1.0 - phi
+    x = np.arange(nx)[None, :] + 0.0 * w
+    y = np.arange(ny)[:, None] + 0.0 * w
+    m = w.sum()
+    area2 = float(np.count_nonzero(phi < 0))
+    per = contour_length(phi, not wall_x, not wall_y)
+
+    def mean(q):
+        return float((w * q).sum() / m) if m > 0 else 0.0
+    return {"mass2": float(m), "xc2": mean(x), "yc2": mean(y),
+            "uc2": mean(fields["ux"]), "vc2": mean(fields["uy"]),
+            "area2": area2, "perimeter": per,
+            "circularity": 2.0 * math.sqrt(math.pi * area2) / per if per > 0 else 0.0}
 
 
 # ---------------------------------------------------------------------------

@@ -176,6 +176,38 @@ def capillary_bubble(kind="bubble", form="STF1", nx=512, ny=1024, W=5.0,
     return Case(f"capillary_{kind}", nx, ny, True, p, phi0, 50000, {"R": R})
 
 
+UG_PHYS = math.sqrt(2 * 0.25 * 0.98)  # reference velocity sqrt(2 R g) of Sec. 5.4, m/s
+
+
+def rising_bubble(form="STF1", nx=120, Ug=0.02, W=4.0, M=0.05, Re=35.0, Eo=10.0,
+                  rho_ratio=10.0, mu_ratio=10.0):
+    """The rising bubble of Sec. 5.4 on an nx x 2nx lattice: the paper's
+    1 m x 2 m box (node spacing 1/nx m, walls half a spacing beyond the
+    outer nodes), no-slip walls at bottom and top, free-slip side walls, a
+    bubble of R = 0.25 m (nx/4 nodes) centred at (0.5 m, 0.5 m), gravity
+    along -y; rho1/rho2 = 10 and mu1/mu2 = 10 (Table test_Paras, so equal
+    kinematic viscosities), Re = rho1 Ug L / mu1 = 35, Eo = rho1 Ug^2 L /
+    sigma = 10 with L = 2R and Ug = sqrt(2 R g).  Ug is the reference
+    velocity in lattice units; the paper gives no mobility or interface
+    width (M, W set here).  meta carries the lattice-to-SI conversions:
+    seconds per step, metres per node, (m/s) per lattice velocity."""
+    R = nx / 4.0
+    L = 2.0 * R
+    nu = Ug * L / Re
+    sigma = Ug * Ug * L / Eo  # rho1 = 1
+    g = Ug * Ug / (2.0 * R)
+    p = dict(sigma=sigma, W=W, M=M, tau_h=1.0, rho1=1.0, rho2=1.0 / rho_ratio,
+             nu1=nu, nu2=nu * rho_ratio / mu_ratio, gx=0.0, gy=-g, form=form)
+    ny = 2 * nx
+    c = 0.5 * nx - 0.5  # node coordinate of 0.5 m
+    dx, dy = _dist(nx, ny, c, c, False, False)
+    phi0 = -np.tanh(2.0 * (R - np.sqrt(dx * dx + dy * dy)) / W)
+    dx_m = 1.0 / nx
+    return Case("rising_bubble", nx, ny, True, p, phi0, 0,
+                {"R": R, "wall_x": True, "m_per_node": dx_m,
+                 "s_per_step": dx_m * Ug / UG_PHYS, "mps_per_lattice": UG_PHYS / Ug})
+
+
 def batch_instances(n=256, seed=0, sizes=(64, 128, 256, 512)):
     """Batched workload: n drop instances, L drawn from `sizes`, R uniform in
     [0.15, 0.35] L, sigma log-uniform in [1e-4, 1e-2], force family cycling
