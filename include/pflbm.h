@@ -137,6 +137,28 @@ typedef struct {
   double nonfinite;   /* number of nodes with a NaN/Inf field */
 } pflbm_diag;
 
+/* Rising-bubble benchmark quantities (Sec. 5.4), lattice units (node
+ * spacing 1, node (x, y) at coordinates x, y).  Fluid 2 (phi = -1) is the
+ * bubble.  The phi = 0 contour is traced by marching squares over the cells
+ * of the node lattice (one cell per node, the node its lower-left corner;
+ * cells wrap in a periodic direction, none lie beyond the last node towards
+ * a wall): a corner is inside when phi < 0, the contour crosses each edge
+ * whose ends differ at the zero of the linear interpolant, and a cell with
+ * four crossings is paired by the sign of its corner mean (inside: the
+ * segments cut off the outside corners). */
+typedef struct {
+  double mass2;       /* sum (1 - phi) */
+  double xc2, yc2;    /* centre of mass: sum (1 - phi) x / mass2, likewise y
+                         (Eq. quantify-yc); 0 when mass2 = 0 */
+  double uc2, vc2;    /* sum (1 - phi) u_x / mass2, likewise u_y: the rise
+                         velocity v_c (Eq. quantify-uc) */
+  double area2;       /* number of nodes with phi < 0 */
+  double perimeter;   /* length of the phi = 0 contour */
+  double circularity; /* 2 sqrt(pi area2) / perimeter (Eq. circularity);
+                         0 without a contour */
+  double nonfinite;   /* nodes with a NaN/Inf phi or u (their cells add nothing) */
+} pflbm_bubble_diag;
+
 /* ---- domain ------------------------------------------------------------ */
 
 /* Bytes of device workspace a domain of nx x ny with this storage needs
@@ -217,6 +239,12 @@ pflbm_status pflbm_read_populations(pflbm_domain* d, float* f_out, float* h_out,
  * struct is still filled). */
 pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom,
                                pflbm_diag* out);
+
+/* Rising-bubble quantities of the current state (FP64 sums of the float32
+ * fields, deterministic order).  Synchronises.  Uses the same workspace
+ * scratch as pflbm_diagnostics.  Returns EUNSTABLE if any node is
+ * non-finite (the struct is still filled); ESTATE before init. */
+pflbm_status pflbm_bubble_diagnostics(pflbm_domain* d, pflbm_bubble_diag* out);
 
 /* Checkpoint / resume: the raw state (populations in their storage format,
  * phi u, step count).  pflbm_state_bytes gives the size of the blob. */

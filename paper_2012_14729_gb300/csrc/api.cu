@@ -625,6 +625,37 @@ pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom, pfl
   return h[12] > 0 ? PFLBM_EUNSTABLE : PFLBM_OK;
 }
 
+pflbm_status pflbm_bubble_diagnostics(pflbm_domain* d, pflbm_bubble_diag* out) {
+  if (!d || !out) return PFLBM_EINVAL;
+  if (!d->has_state) return PFLBM_ESTATE;
+  pflbm_status st = stage_fields(d);
+  if (st != PFLBM_OK) return st;
+  StepArgs a = make_args(d, d->cur);
+  double* red = reinterpret_cast<double*>(d->ws + d->lay.red);
+  double* part = reinterpret_cast<double*>(d->ws + d->lay.partials);
+  cudaError_t e = launch_bubble_diag(a.L, a.fields, part, kMaxDiagBlocks, red, d->stream);
+  double h[kNRed];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) {
+    set_err("bubble diagnostics", e);
+    return PFLBM_ECUDA;
+  }
+  memset(out, 0, sizeof(*out));
+  out->mass2 = h[0];
+  if (h[0] > 0) {
+    out->xc2 = h[1] / h[0];
+    out->yc2 = h[2] / h[0];
+    out->uc2 = h[3] / h[0];
+    out->vc2 = h[4] / h[0];
+  }
+  out->area2 = h[5];
+  out->perimeter = h[6];
+  out->circularity = h[6] > 0 ? 2.0 * sqrt(M_PI * h[5]) / h[6] : 0.0;
+  out->nonfinite = h[7];
+  return h[7] > 0 ? PFLBM_EUNSTABLE : PFLBM_OK;
+}
+
 size_t pflbm_state_bytes(const pflbm_domain* d) {
   if (!d) return 0;
   // header (step count, magic) + the current population buffers + phi u

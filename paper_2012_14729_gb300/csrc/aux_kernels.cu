@@ -202,19 +202,113 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
 }
 
 // One warp per slot: lanes take block partials in a fixed stride and the
-// warp combines them by shuffles (deterministic order).
-__global__ void k_diag_final(const double* __restrict__ partials, int nblocks,
-                             double* __restrict__ out) {
+// warp combines them by shuffles (deterministic order).  Slots below nslots
+// are summed, except max_slot (a maximum); the rest come out as 0.
+__global__ void k_diag_final(const double* __restrict__ partials, int nblocks, int nslots,
+                             int max_slot, double* __restrict__ out) {
   const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j >= kNRed) return;
+  const bool is_max = j == max_slot;
   double v = 0.0;
-  if (j < 13)
+  if (j < nslots)
     for (int b = lane; b < nblocks; b += 32) {
       const double p = partials[b * kNRed + j];
-      v = (j == 1) ? fmax(v, p) : v + p;
+      v = is_max ? fmax(v, p) : v + p;
     }
-  v = (j == 1) ? warp_max(v) : warp_sum(v);
+  v = is_max ? warp_max(v) : warp_sum(v);
   if (lane == 0) out[j] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Rising-bubble quantities (Sec. 5.4).  Each thread takes nodes and, with
+// each node, the lattice cell whose lower-left corner it is (cells wrap in a
+// periodic direction; there is none beyond the last node towards a wall).
+// Slots: 0 sum (1 - phi), 1 sum (1 - phi) x, 2 sum (1 - phi) y,
+// 3 sum (1 - phi) u_x, 4 sum (1 - phi) u_y, 5 nodes with phi < 0,
+// 6 phi = 0 contour length, 7 non-finite count.
+// ---------------------------------------------------------------------------
+constexpr int kBubbleSlots = 8;
+
+// Contour length in one cell by marching squares.  Corners c0..c3 at
+// (0,0), (1,0), (1,1), (0,1); inside means phi < 0; on an edge whose ends
+// differ the contour passes the zero of the linear interpolant.  Four
+// crossings (a saddle) are paired by the sign of the corner mean: inside,
+// the segments cut off the two outside corners, else the two inside ones.
+__device__ double cell_contour(double c0, double c1, double c2, double c3) {
+  const bool i0 = c0 < 0.0, i1 = c1 < 0.0, i2 = c2 < 0.0, i3 = c3 < 0.0;
+  const bool k0 = i0 != i1, k1 = i1 != i2, k2 = i2 != i3, k3 = i3 != i0;
+  // crossing points, used only on cut edges: E0 on (0,0)-(1,0), E1 on
+  // (1,0)-(1,1), E2 on (1,1)-(0,1), E3 on (0,1)-(0,0)
+  const double e0x = c0 / (c0 - c1), e0y = 0.0;
+  const double e1x = 1.0, e1y = c1 / (c1 - c2);
+  const double e2x = 1.0 - c2 / (c2 - c3), e2y = 1.0;
+  const double e3x = 0.0, e3y = 1.0 - c3 / (c3 - c0);
+  if (k0 && k1 && k2 && k3) {
+    const bool centre_in = ((c0 + c1) + c2) + c3 < 0.0;
+    double len = 0.0;  // corner k lies between edges k-1 and k
+    if (i0 != centre_in) len += hypot(e3x - e0x, e3y - e0y);
+    if (i1 != centre_in) len += hypot(e0x - e1x, e0y - e1y);
+    if (i2 != centre_in) len += hypot(e1x - e2x, e1y - e2y);
+    if (i3 != centre_in) len += hypot(e2x - e3x, e2y - e3y);
+    return len;
+  }
+  if (k0 && k1) return hypot(e0x - e1x, e0y - e1y);
+  if (k0 && k2) return hypot(e0x - e2x, e0y - e2y);
+  if (k0 && k3) return hypot(e0x - e3x, e0y - e3y);
+  if (k1 && k2) return hypot(e1x - e2x, e1y - e2y);
+  if (k1 && k3) return hypot(e1x - e3x, e1y - e3y);
+  if (k2 && k3) return hypot(e2x - e3x, e2y - e3y);
+  return 0.0;
+}
+
+__global__ void __launch_bounds__(kDiagThreads) k_bubble_partial(const Lattice L,
+                                                                 const float* __restrict__ fields,
+                                                                 double* __restrict__ partials) {
+  const int n = L.nx * L.ny;
+  double acc[kBubbleSlots];
+#pragma unroll
+  for (int j = 0; j < kBubbleSlots; ++j) acc[j] = 0.0;
+  const float* __restrict__ phi = fields;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int y = k / L.nx, x = k - y * L.nx;
+    const double p = phi[k];
+    const double ux = fields[2 * n + k], uy = fields[3 * n + k];
+    if (!(isfinite(p) && isfinite(ux) && isfinite(uy))) {
+      acc[7] += 1.0;
+      continue;
+    }
+    const double w = 1.0 - p;
+    acc[0] += w;
+    acc[1] += w * x;
+    acc[2] += w * y;
+    acc[3] += w * ux;
+    acc[4] += w * uy;
+    acc[5] += p < 0.0 ? 1.0 : 0.0;
+    const bool has_cell = (x + 1 < L.nx || !L.wall_x) && (y + 1 < L.ny || !L.wall);
+    if (has_cell) {
+      const int x1 = x + 1 < L.nx ? x + 1 : 0;
+      const int r1 = (y + 1 < L.ny ? y + 1 : 0) * L.nx;
+      const double c1 = phi[y * L.nx + x1], c2 = phi[r1 + x1], c3 = phi[r1 + x];
+      const double lo = fmin(fmin(p, c1), fmin(c2, c3)), hi = fmax(fmax(p, c1), fmax(c2, c3));
+      // a non-finite corner is counted at its own node; its cells add nothing
+      if (lo < 0.0 && hi >= 0.0 && isfinite(c1) && isfinite(c2) && isfinite(c3))
+        acc[6] += cell_contour(p, c1, c2, c3);
+    }
+  }
+  __shared__ double red[kDiagThreads / 32][kBubbleSlots];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kBubbleSlots; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[wid][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kBubbleSlots) {
+    const int j = threadIdx.x;
+    double v = red[0][j];
+    for (int w = 1; w < kDiagThreads / 32; ++w) v += red[w][j];
+    partials[blockIdx.x * kNRed + j] = v;
+  }
 }
 
 int diag_blocks(int n_nodes, int max_blocks) {
@@ -227,7 +321,15 @@ cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, doubl
                         int max_blocks, double* red, cudaStream_t s) {
   const int nb = diag_blocks(L.nx * L.ny, max_blocks);
   k_diag_partial<<<nb, kDiagThreads, 0, s>>>(L, fields, g, partials);
-  k_diag_final<<<1, 32 * kNRed, 0, s>>>(partials, nb, red);
+  k_diag_final<<<1, 32 * kNRed, 0, s>>>(partials, nb, 13, 1, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bubble_diag(const Lattice& L, const float* fields, double* partials,
+                               int max_blocks, double* red, cudaStream_t s) {
+  const int nb = diag_blocks(L.nx * L.ny, max_blocks);
+  k_bubble_partial<<<nb, kDiagThreads, 0, s>>>(L, fields, partials);
+  k_diag_final<<<1, 32 * kNRed, 0, s>>>(partials, nb, kBubbleSlots, -1, red);
   return cudaGetLastError();
 }
 

@@ -163,6 +163,10 @@ struct DiagGeom {
 cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, double* partials,
                         int max_blocks, double* red, cudaStream_t s);
 int diag_blocks(int n_nodes, int max_blocks);
+// Rising-bubble sums of the staged fields (fluid-2 moments, phi < 0 count,
+// marching-squares contour length) into red[0..7].
+cudaError_t launch_bubble_diag(const Lattice& L, const float* fields, double* partials,
+                               int max_blocks, double* red, cudaStream_t s);
 
 // Message returned by pflbm_last_error() on this thread.
 void set_last_error(const char* msg);

@@ -62,6 +62,14 @@ class pflbm_diag(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pflbm_bubble_diag(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "mass2", "xc2", "yc2", "uc2", "vc2", "area2", "perimeter", "circularity", "nonfinite")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # every symbol include/pflbm.h declares, with its ctypes signature
 _vp, _i, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
 SIGNATURES = {
@@ -80,6 +88,7 @@ SIGNATURES = {
     "pflbm_read_fields": (_i, [_vp, _vp, _i]),
     "pflbm_read_populations": (_i, [_vp, _vp, _vp, _i]),
     "pflbm_diagnostics": (_i, [_vp, ctypes.POINTER(pflbm_diag_geom), ctypes.POINTER(pflbm_diag)]),
+    "pflbm_bubble_diagnostics": (_i, [_vp, ctypes.POINTER(pflbm_bubble_diag)]),
     "pflbm_state_bytes": (_sz, [_vp]),
     "pflbm_save_state": (_i, [_vp, _vp, _i]),
     "pflbm_load_state": (_i, [_vp, _vp, _i]),
@@ -224,6 +233,14 @@ def pflbm_diagnostics(d, geom: Optional[pflbm_diag_geom]):
                                   ctypes.byref(out))
     if st not in (0, 4):
         _check(st, "pflbm_diagnostics")
+    return st, out
+
+
+def pflbm_bubble_diagnostics(d):
+    out = pflbm_bubble_diag()
+    st = load().pflbm_bubble_diagnostics(d, ctypes.byref(out))
+    if st not in (0, 4):
+        _check(st, "pflbm_bubble_diagnostics")
     return st, out
 
 
@@ -470,6 +487,13 @@ class Domain:
         if xc is not None:
             geom = pflbm_diag_geom(xc, yc, r_in, r_out)
         st, d = pflbm_diagnostics(self.h, geom)
+        out = d.as_dict()
+        out["status"] = STATUS[st]
+        return out
+
+    def bubble_diagnostics(self):
+        """Rising-bubble quantities (Sec. 5.4) in lattice units."""
+        st, d = pflbm_bubble_diagnostics(self.h)
         out = d.as_dict()
         out["status"] = STATUS[st]
         return out
