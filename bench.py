@@ -80,11 +80,39 @@ def make_case(name: str, form: str):
     if name == "bubble_2048x1024":
         # 4x the default's nodes, state 0.34 GB per buffer (> L2): DRAM traffic capture
         return wl.capillary_bubble("bubble", form=form, nx=1024, ny=2048, R=128.0)
+    if name == "rising_bubble_120x240":
+        # Sec. 5.4 geometry: free-slip side walls, no-slip top and bottom
+        return wl.rising_bubble(form=form, nx=120)
+    if name == "rising_bubble_2048x4096":
+        # the same geometry at 8.4 M nodes (state 1.34 GB per step, > L2)
+        return wl.rising_bubble(form=form, nx=2048)
     if name == "drop_64x64":
         return wl.stationary_drop(form)
     if name == "merging_256x128":
         return wl.merging_drops(form)
     raise SystemExit(f"unknown workload {name}")
+
+
+def walls_name(case) -> str:
+    w = ["x free-slip"] if case.meta.get("wall_x", False) else []
+    if case.wall_y:
+        w.append("y")
+    return "+".join(w) if w else "none"
+
+
+def time_bubble_diagnostics(dom, case, calls=20):
+    """Wall time of one pflbm_bubble_diagnostics call (field staging, the
+    FP64 reduction over nodes and cells, the read-back of 8 sums; it
+    synchronises), mean over `calls`, with the quantities in SI units."""
+    dom.bubble_diagnostics()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        g = dom.bubble_diagnostics()
+    ms = (time.perf_counter() - t0) / calls * 1e3
+    m = case.meta
+    return {"ms_per_call": ms, "calls": calls, "status": g["status"],
+            "yc_m": (g["yc2"] + 0.5) * m["m_per_node"], "vc_mps": g["vc2"] * m["mps_per_lattice"],
+            "circularity": g["circularity"]}
 
 
 def measured_peaks():
@@ -212,7 +240,8 @@ def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2, threads=None):
     import oracle
     threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
-    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0)
+    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0,
+                   wall_x=case.meta.get("wall_x", False))
     s.step(1)  # first step separately (first-step flag), untimed
     t0 = time.perf_counter()
     n = 0
@@ -230,7 +259,8 @@ def run_reference(args, case):
     import oracle
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0)
+    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0,
+                   wall_x=case.meta.get("wall_x", False))
     s.step(args.warmup)
     t0 = time.perf_counter()
     s.step(args.steps)
@@ -242,7 +272,7 @@ def run_reference(args, case):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "nx": case.nx, "ny": case.ny,
-                   "form": args.form, "walls": "y" if case.wall_y else "none"},
+                   "form": args.form, "walls": walls_name(case)},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle",
                          "sample": f"{args.warmup}+{args.steps} full-grid oracle steps"},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
@@ -265,7 +295,9 @@ def run_ours(args, case):
     pflbm.load()
 
     n_nodes = case.nx * case.ny
-    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage, device=dev)
+    wall_x = case.meta.get("wall_x", False)
+    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, wall_x=wall_x, storage=args.storage,
+                       device=dev)
     dom.set_params(**case.params)
     dom.init_phi(case.phi0.astype(np.float32))
     if args.stage == "auto":
@@ -329,8 +361,8 @@ def run_ours(args, case):
     phi_host = torch.from_numpy(case.phi0.astype(np.float32)).pin_memory()
     out_host = torch.empty((len(pflbm.FIELDS), case.ny, case.nx), dtype=torch.float32,
                            pin_memory=True)
-    e2e_dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage,
-                           device=dev, stream=stream)
+    e2e_dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, wall_x=wall_x,
+                           storage=args.storage, device=dev, stream=stream)
     e2e_dom.set_params(**case.params)
     e2e_dom.stage_mode(stage)
     torch.cuda.synchronize()
@@ -372,7 +404,8 @@ def run_ours(args, case):
 
     # the same physics on a grid whose state exceeds L2 (8.4 M nodes, 1.34 GB
     # per step), timed over consecutive steps without flushing
-    l2x = measure_l2_exceeding(args, dev) if ws == 1 and not args.no_l2x else None
+    l2x = (measure_l2_exceeding(args, dev, wall_x=wall_x)
+           if ws == 1 and not args.no_l2x and case.nx * case.ny < (1 << 23) else None)
 
     line = {
         "metric": "GLUPS (coupled f+h step)", "value": value, "unit": "GLUPS",
@@ -380,7 +413,7 @@ def run_ours(args, case):
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "nx": case.nx, "ny": case.ny,
-                   "walls": "y" if case.wall_y else "none", "form": args.form,
+                   "walls": walls_name(case), "form": args.form,
                    "storage": args.storage, "stage": stage,
                    "l2": "flushed before every timed step (256 MB written, then 256 MB "
                          "read: no line of the state and no dirty line left in L2)",
@@ -393,21 +426,25 @@ def run_ours(args, case):
     }
     if l2x is not None:
         line["l2_exceeding"] = l2x
+    if wall_x:
+        line["bubble_diagnostics"] = time_bubble_diagnostics(dom, case)
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def measure_l2_exceeding(args, dev, steps=30):
+def measure_l2_exceeding(args, dev, steps=30, wall_x=False):
     """GLUPS and roofline fraction of the step on the 2048 x 4096 rising
-    bubble (same physics as the default workload, state larger than L2)."""
+    bubble (same physics as the default workload, state larger than L2);
+    with free-slip side walls when the timed workload has them."""
     import torch
     from paper_2012_14729_gb300 import pflbm
-    name = "bubble_4096x2048"
+    name = "rising_bubble_2048x4096" if wall_x else "bubble_4096x2048"
     case = make_case(name, args.form)
     n = case.nx * case.ny
-    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, storage=args.storage, device=dev)
+    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y, wall_x=wall_x, storage=args.storage,
+                       device=dev)
     dom.set_params(**case.params)
     dom.init_phi(case.phi0.astype(np.float32))
     stage = dom.autotune(5)

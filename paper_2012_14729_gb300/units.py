@@ -8,7 +8,12 @@ Uc (lattice units), the groups are
     Re = rho1 Uc Lc / mu1        Pe = Uc Lc / (4 M beta)     We = rho1 Lc Uc^2 / sigma
     Fr = Uc / sqrt(g Lc)         Cn = W / Lc
 
-with beta = 3 sigma / (4 W) the free-energy coefficient (Sec. 2.1).
+with beta = 3 sigma / (4 W) the free-energy coefficient (Sec. 2.1).  The
+rising bubble (Sec. 5.4) is stated with Re and the Eotvos and Morton numbers
+
+    Eo = rho1 g Lc^2 / sigma     Mo = Eo^3 / Re^4 = g mu1^4 / (rho1 sigma^3)
+
+which are We and Re with the gravity velocity Uc = sqrt(g Lc) (Fr = 1).
 """
 from __future__ import annotations
 
@@ -43,7 +48,9 @@ def groups(p: dict, Lc: float, Uc: float) -> dict:
     beta = 3.0 * p["sigma"] / (4.0 * p["W"])
     mu1 = p["rho1"] * p["nu1"]
     g = math.hypot(p.get("gx", 0.0), p.get("gy", 0.0))
+    Eo = p["rho1"] * g * Lc * Lc / p["sigma"]
     return dict(Re=p["rho1"] * Uc * Lc / mu1, Pe=Uc * Lc / (4.0 * p["M"] * beta),
                 We=p["rho1"] * Lc * Uc * Uc / p["sigma"],
                 Fr=(Uc / math.sqrt(g * Lc)) if g > 0 else math.inf, Cn=p["W"] / Lc,
-                rho_ratio=p["rho1"] / p["rho2"], mu_ratio=mu1 / (p["rho2"] * p["nu2"]))
+                rho_ratio=p["rho1"] / p["rho2"], mu_ratio=mu1 / (p["rho2"] * p["nu2"]),
+                Eo=Eo, Mo=g * mu1 ** 4 / (p["rho1"] * p["sigma"] ** 3))

@@ -179,7 +179,7 @@ def capillary_bubble(kind="bubble", form="STF1", nx=512, ny=1024, W=5.0,
 UG_PHYS = math.sqrt(2 * 0.25 * 0.98)  # reference velocity sqrt(2 R g) of Sec. 5.4, m/s
 
 
-def rising_bubble(form="STF1", nx=120, Ug=0.02, W=4.0, M=0.05, Re=35.0, Eo=10.0,
+def rising_bubble(form="STF1", nx=120, Ug=0.01, W=8.0, M=0.05, tau_h=0.8, Re=35.0, Eo=10.0,
                   rho_ratio=10.0, mu_ratio=10.0):
     """The rising bubble of Sec. 5.4 on an nx x 2nx lattice: the paper's
     1 m x 2 m box (node spacing 1/nx m, walls half a spacing beyond the
@@ -188,15 +188,19 @@ def rising_bubble(form="STF1", nx=120, Ug=0.02, W=4.0, M=0.05, Re=35.0, Eo=10.0,
     along -y; rho1/rho2 = 10 and mu1/mu2 = 10 (Table test_Paras, so equal
     kinematic viscosities), Re = rho1 Ug L / mu1 = 35, Eo = rho1 Ug^2 L /
     sigma = 10 with L = 2R and Ug = sqrt(2 R g).  Ug is the reference
-    velocity in lattice units; the paper gives no mobility or interface
-    width (M, W set here).  meta carries the lattice-to-SI conversions:
-    seconds per step, metres per node, (m/s) per lattice velocity."""
+    velocity in lattice units; the paper gives no mobility, interface width
+    or tau_h.  The defaults are the ones every force form runs to t = 3 s
+    with at 120 x 240: with W = 4, 5 or 6 phi undershoots -1 inside the
+    light bubble until its density reaches zero and the run diverges
+    (STF-1 at W = 4 after ~2400 steps, in the FP64 oracle as on the GPU).
+    meta carries the lattice-to-SI conversions: seconds per step, metres
+    per node, (m/s) per lattice velocity."""
     R = nx / 4.0
     L = 2.0 * R
     nu = Ug * L / Re
     sigma = Ug * Ug * L / Eo  # rho1 = 1
     g = Ug * Ug / (2.0 * R)
-    p = dict(sigma=sigma, W=W, M=M, tau_h=1.0, rho1=1.0, rho2=1.0 / rho_ratio,
+    p = dict(sigma=sigma, W=W, M=M, tau_h=tau_h, rho1=1.0, rho2=1.0 / rho_ratio,
              nu1=nu, nu2=nu * rho_ratio / mu_ratio, gx=0.0, gy=-g, form=form)
     ny = 2 * nx
     c = 0.5 * nx - 0.5  # node coordinate of 0.5 m

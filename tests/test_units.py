@@ -32,3 +32,27 @@ def test_capillary_wave_groups_of_the_paper():
 def test_rejects_non_positive_groups():
     with pytest.raises(ValueError):
         units.lattice_params(Lc=64, Uc=0.01, Re=0, We=1, Cn=0.1)
+
+
+def test_rising_bubble_groups_of_the_paper():
+    """Sec. 5.4, Table test_Paras: rho1 = 1000, mu1 = 10, g = 0.98, sigma =
+    24.5, R = 0.25 with L = 2R and Ug = sqrt(2 R g) give Re = 35, Eo = 10 and
+    Mo = Eo^3 / Re^4; the lattice workload keeps those groups."""
+    from paper_2012_14729_gb300 import workloads as wl
+    si = dict(rho1=1000.0, rho2=100.0, nu1=10.0 / 1000.0, nu2=1.0 / 100.0, sigma=24.5,
+              W=0.01, M=1.0, gx=0.0, gy=-0.98)
+    Ug = math.sqrt(2 * 0.25 * 0.98)
+    g = units.groups(si, Lc=0.5, Uc=Ug)
+    assert g["Re"] == pytest.approx(35.0) and g["Eo"] == pytest.approx(10.0)
+    assert g["Mo"] == pytest.approx(10.0 ** 3 / 35.0 ** 4)
+    assert g["Fr"] == pytest.approx(1.0) and g["We"] == pytest.approx(g["Eo"])
+    assert g["rho_ratio"] == pytest.approx(10.0) and g["mu_ratio"] == pytest.approx(10.0)
+    for nx in (120, 240):
+        c = wl.rising_bubble("STF1", nx=nx)
+        gl = units.groups(c.params, Lc=nx / 2, Uc=math.sqrt(-c.params["gy"] * nx / 2))
+        for k in ("Re", "Eo", "Mo", "rho_ratio", "mu_ratio"):
+            assert gl[k] == pytest.approx(g[k], rel=1e-12), k
+        assert gl["Fr"] == pytest.approx(1.0)
+        # one second is 1 / s_per_step steps; U_g in SI is Ug lattice x (m/s per lattice)
+        assert c.meta["mps_per_lattice"] * math.sqrt(-c.params["gy"] * nx / 2) == \
+            pytest.approx(Ug)
