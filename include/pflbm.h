@@ -163,7 +163,9 @@ typedef struct {
 
 /* Bytes of device workspace a domain of nx x ny with this storage needs
  * (populations double-buffered with one ghost row above and below, phi u,
- * field staging and reduction scratch).  0 for invalid sizes. */
+ * field staging and reduction scratch).  0 for invalid sizes: nx, ny >= 4
+ * and 9 (ny + 2) nx < 2^31 (population planes use 32-bit offsets; about
+ * 238 M nodes). */
 size_t pflbm_workspace_bytes(int nx, int ny, pflbm_storage storage);
 
 /* Create a domain over a caller-owned device workspace (256-byte aligned,
@@ -260,7 +262,9 @@ void pflbm_destroy(pflbm_domain* d);
  * segment of ckpt_every steps but the last, the tape of one segment (24
  * float32 planes of nx * ny per step: pulled f, phi, grad phi, lap phi, mu,
  * force values, u, P, div(phi u), d_t(phi u)), two adjoint states and work
- * planes.  0 for invalid input (FP32 storage only). */
+ * planes.  0 for invalid input: FP32 storage, periodic x, nsteps and
+ * ckpt_every >= 1, and 24 nx ny < 2^31 (the tape's 32-bit plane offsets;
+ * about 89 M nodes). */
 size_t pflbm_adjoint_scratch_bytes(const pflbm_domain* d, int nsteps, int ckpt_every);
 
 /* Run nsteps steps from phi0 (device [ny][nx]) with the domain's parameters,

@@ -759,6 +759,8 @@ struct AdjLayout {
 bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
   if (!d || nsteps < 1 || every < 1 || d->storage != kFP32 || d->wall_x) return false;
   const size_t n = (size_t)d->nx * d->ny;
+  // the taping step addresses its planes with 32-bit offsets
+  if ((size_t)kTapePlanes * n >= ((size_t)1 << 31)) return false;
   L->blob = align_up(pflbm_state_bytes(d));
   L->ncp = (nsteps + every - 1) / every;
   size_t off = 0;

@@ -99,3 +99,22 @@ def test_noalloc_diagnostics_size_checks(lib):
     assert "8392704 nodes" in msg and "at most 8388608 nodes" in msg
     hdr = open(HEADER).read()
     assert re.search(r"#define PFLBM_NOALLOC_MAX_NODES\s+%d\b" % pflbm.NOALLOC_MAX_NODES, hdr)
+
+
+def test_size_limits_of_32_bit_plane_offsets(lib):
+    """Sizes whose plane offsets would not fit 32 bits are refused on the
+    host: the population planes (9 (ny + 2) nx < 2^31) and the adjoint's tape
+    (24 nx ny < 2^31).  No CUDA call: create never touches the workspace."""
+    from paper_2012_14729_gb300 import pflbm
+    assert pflbm.pflbm_workspace_bytes(16384, 14560, 0) > 0      # 9 * 14562 * 16384 < 2^31
+    assert pflbm.pflbm_workspace_bytes(16384, 14564, 0) == 0     # >= 2^31
+    assert pflbm.pflbm_workspace_bytes(14564, 16384, 1) == 0
+    fake = 1 << 20
+    for ny, ok in ((5461, True), (5462, False)):                 # 24 * 16384 * ny vs 2^31
+        nbytes = pflbm.pflbm_workspace_bytes(16384, ny, 0)
+        d = pflbm.pflbm_create(16384, ny, 0, 1, 0, fake, nbytes, None)
+        try:
+            got = lib.pflbm_adjoint_scratch_bytes(d, 10, 5)
+            assert (got > 0) == ok, (ny, got)
+        finally:
+            pflbm.pflbm_destroy(d)
