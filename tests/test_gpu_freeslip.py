@@ -88,3 +88,43 @@ def test_side_walls_refuse_x_forcing_and_boxes(pf):
         d.stage_mode("boxes")
     d.init_phi(wl.drop(40, 40, 8.0, 4.0, periodic_y=False).astype(np.float32))
     assert d.autotune(2) == "gather"
+
+
+@pytest.mark.parametrize("storage,tol_phi,tol_u", [("fp16", 2e-4, 2e-5), ("bf16", 2e-3, 2e-4)])
+def test_side_walls_with_16bit_storage(pf, orc, storage, tol_phi, tol_u):
+    """16-bit population storage through the specular pulls: error against
+    the FP64 oracle at the 16-bit bars of the periodic storage tests."""
+    nx, ny = 70, 45
+    phi0 = wl.drop(nx, ny, 10.0, 4.0, xc=4.3, yc=21.6, periodic_y=False)
+    p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.25, nu1=0.1, nu2=0.2, gy=-1e-5,
+             form="CSF1")
+    d = pf.Domain(nx, ny, wall_y=True, wall_x=True, storage=storage).set_params(**p)
+    d.init_phi(phi0.astype(np.float32))
+    d.step(200)
+    g = d.fields()
+    o = orc.Sim(nx, ny, True, orc.Params(**p), phi0.astype(np.float32).astype(np.float64),
+                wall_x=True).step(200).macro()
+    e = (_err(g, o, "phi"), _err(g, o, "ux"), _err(g, o, "uy"))
+    assert e[0] <= tol_phi and max(e[1:]) <= tol_u, e
+
+
+def test_side_walls_state_round_trip_and_refusals(pf):
+    nx, ny = 48, 40
+    p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.5, nu1=0.1, nu2=0.1, gy=-1e-5)
+    phi0 = wl.drop(nx, ny, 8.0, 4.0, xc=3.0, yc=20.0, periodic_y=False).astype(np.float32)
+    a = pf.Domain(nx, ny, wall_y=True, wall_x=True).set_params(**p).init_phi(phi0)
+    a.step(20)
+    blob = a.save_state()
+    a.step(30)
+    b = pf.Domain(nx, ny, wall_y=True, wall_x=True).set_params(**p).load_state(blob)
+    b.step(30)
+    for k, v in a.fields().items():
+        np.testing.assert_array_equal(v, b.fields()[k])
+    # a side-wall state does not load into a periodic-x domain
+    c = pf.Domain(nx, ny, wall_y=True).set_params(**p)
+    with pytest.raises(pf.PflbmError):
+        c.load_state(blob)
+    # the batch and the adjoint take periodic x only
+    with pytest.raises(pf.PflbmError):
+        pf.Batch([a])
+    assert pf.pflbm_adjoint_scratch_bytes(a.h, 10, 5) == 0
