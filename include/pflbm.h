@@ -249,7 +249,12 @@ pflbm_status pflbm_diagnostics(pflbm_domain* d, const pflbm_diag_geom* geom,
 pflbm_status pflbm_bubble_diagnostics(pflbm_domain* d, pflbm_bubble_diag* out);
 
 /* Checkpoint / resume: the raw state (populations in their storage format,
- * phi u, step count).  pflbm_state_bytes gives the size of the blob. */
+ * phi u, step count, and the mean of phi0 from which the default rho0
+ * follows).  pflbm_state_bytes gives the size of the blob.  Loading needs
+ * the parameters set first; when they leave rho0 to the library (NaN), the
+ * resumed run takes rho0 = rho(mean phi0) of the run that saved the blob,
+ * with the current rho1, rho2.  Errors: EINVAL for a blob of another size,
+ * storage or boundary kind, ESTATE without parameters, ECUDA. */
 size_t pflbm_state_bytes(const pflbm_domain* d);
 pflbm_status pflbm_save_state(pflbm_domain* d, void* dst, int on_device);
 pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device);

@@ -25,6 +25,9 @@ void set_msg(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxDiagBlocks = 1024;
+// state blob magics: without / with the mean of phi0 in the header
+constexpr long long kStateMagic = 0x70666c626d;
+constexpr long long kStateMagicMean = 0x70666c626e;
 constexpr int kGraphSteps = 64;  // steps captured per graph (even)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -88,9 +91,19 @@ struct pflbm_domain {
   int graphs;
   cudaGraphExec_t gexec;
   int g_parity;  // buffer parity the captured graph starts from
+  // mean of phi0 over the lattice (the run's initial condition), from which
+  // the default background density rho0 = rho(mean phi0) follows
+  int has_mean_phi0;
+  double mean_phi0;
 };
 
 namespace {
+
+// rho is linear in phi, so the mean initial density is rho(mean phi0)
+float default_rho0(const pflbm_domain* d) {
+  const double m = d->mean_phi0;
+  return (float)(0.5 * d->par.rho1 * (1 + m) + 0.5 * d->par.rho2 * (1 - m));
+}
 
 bool is_pow2(double v) {
   if (!(v > 0) || !isfinite(v)) return false;
@@ -350,6 +363,7 @@ pflbm_status pflbm_set_params(pflbm_domain* d, const pflbm_params* p) {
   q.gx = (float)p->gx;
   q.gy = (float)p->gy;
   q.rho0 = isnan(p->rho0) ? q.rho_mid : (float)p->rho0;  // refined at init
+  if (isnan(p->rho0) && d->has_mean_phi0) q.rho0 = default_rho0(d);
   q.uwb = (float)p->uw_bottom;
   q.uwt = (float)p->uw_top;
   q.inv_tau_h = (float)(1.0 / th);
@@ -407,8 +421,11 @@ pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
       set_err("init mean density", e);
       return PFLBM_ECUDA;
     }
-    const double mphi = h[0] / (double)n;
-    d->phys.rho0 = (float)(0.5 * d->par.rho1 * (1 + mphi) + 0.5 * d->par.rho2 * (1 - mphi));
+    d->mean_phi0 = h[0] / (double)n;
+    d->has_mean_phi0 = 1;
+    d->phys.rho0 = default_rho0(d);
+  } else {
+    d->has_mean_phi0 = 0;
   }
   e = cudaMemsetAsync(d->ws + d->lay.err, 0, 4, d->stream);
   if (e != cudaSuccess) {
@@ -667,7 +684,11 @@ pflbm_status pflbm_save_state(pflbm_domain* d, void* dst, int on_device) {
   if (!d || !dst) return PFLBM_EINVAL;
   if (!d->has_state) return PFLBM_ESTATE;
   const Layout& L = d->lay;
-  long long hdr[8] = {0x70666c626d, d->t, d->nx, d->ny, d->storage, d->wall, d->wall_x, 0};
+  // header: magic, step, nx, ny, storage, walls y and x, and (second magic)
+  // the bits of mean phi0 that the default rho0 of the run follows from
+  long long hdr[8] = {d->has_mean_phi0 ? kStateMagicMean : kStateMagic, d->t, d->nx, d->ny,
+                      d->storage, d->wall, d->wall_x, 0};
+  if (d->has_mean_phi0) memcpy(&hdr[7], &d->mean_phi0, sizeof(double));
   char* p = (char*)dst;
   const cudaMemcpyKind h2x = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
   const cudaMemcpyKind d2x = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -703,8 +724,8 @@ pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device) {
     set_err("load_state", e);
     return PFLBM_ECUDA;
   }
-  if (hdr[0] != 0x70666c626d || hdr[2] != d->nx || hdr[3] != d->ny || hdr[4] != d->storage ||
-      hdr[5] != d->wall || hdr[6] != d->wall_x) {
+  if ((hdr[0] != kStateMagic && hdr[0] != kStateMagicMean) || hdr[2] != d->nx ||
+      hdr[3] != d->ny || hdr[4] != d->storage || hdr[5] != d->wall || hdr[6] != d->wall_x) {
     set_msg("pflbm_load_state: state does not match this domain");
     return PFLBM_EINVAL;
   }
@@ -732,6 +753,11 @@ pflbm_status pflbm_load_state(pflbm_domain* d, const void* src, int on_device) {
   build_maps(d);
   d->t = hdr[1];
   d->has_state = 1;
+  d->has_mean_phi0 = hdr[0] == kStateMagicMean;
+  if (d->has_mean_phi0) {
+    memcpy(&d->mean_phi0, &hdr[7], sizeof(double));
+    if (isnan(d->par.rho0)) d->phys.rho0 = default_rho0(d);
+  }
   drop_graph(d);
   return PFLBM_OK;
 }

@@ -132,6 +132,30 @@ def test_deterministic_and_graph_equal(pf):
         np.testing.assert_array_equal(h, outs[0][1])
 
 
+def test_checkpoint_resume_keeps_the_default_rho0(pf):
+    """With gravity, F_g = (rho - rho0) g depends on rho0, which by default
+    is the mean density of phi0: the blob carries it, so a resumed run
+    continues bitwise even though the resuming domain never saw phi0."""
+    nx, ny = 64, 48
+    phi0 = wl.bubble(nx, ny, 10.0, 4.0).astype(np.float32)
+    p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.2, nu1=0.1, nu2=0.1, gy=-1e-5)
+    a = pf.Domain(nx, ny, wall_y=True).set_params(**p).init_phi(phi0)
+    a.step(30)
+    blob = a.save_state()
+    a.step(40)
+    b = pf.Domain(nx, ny, wall_y=True).set_params(**p).load_state(blob)
+    b.step(40)
+    for x, y in zip(a.populations(), b.populations()):
+        np.testing.assert_array_equal(x, y)
+    # parameters set again after the resume keep the run's rho0 as well
+    b.set_params(**p)
+    a.set_params(**p)
+    a.step(5)
+    b.step(5)
+    for x, y in zip(a.populations(), b.populations()):
+        np.testing.assert_array_equal(x, y)
+
+
 def test_checkpoint_resume_bitwise(pf):
     c = wl.stationary_drop("PF2")
     a = pf.Domain(c.nx, c.ny).set_params(**c.params).init_phi(c.phi0.astype(np.float32))
