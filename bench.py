@@ -593,7 +593,7 @@ def run_batch(args):
     nodes = sum(c.nx * c.ny for c in cases)
     b = pflbm.Batch(doms, stream=stream)
     b.step(1)
-    mode, cps = b.autotune(3)
+    mode, cps, rows = b.autotune(3)
     b.graphs(True)
     b.step(args.warmup)
     b.synchronize()
@@ -636,7 +636,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "instances": len(cases), "nodes": nodes,
-                   "stage": mode, "ctas_per_sm": cps, "graphs": True,
+                   "stage": mode, "ctas_per_sm": cps, "tile": f"32x{rows}", "graphs": True,
                    "l2": f"state {160 * nodes / 2**30:.2f} GiB per step (L2 is 129 MB)",
                    "state_status": diag["status"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -319,13 +319,25 @@ pflbm_status pflbm_batch_step(pflbm_batch* b, int nsteps);
 pflbm_status pflbm_batch_set_graphs(pflbm_batch* b, int enable);
 
 /* Staging mode (PFLBM_STAGE_*) and persistent CTAs per SM of the batch
- * kernel; pflbm_batch_autotune times trial steps of each candidate on the
- * current states (which stay unchanged) and keeps the fastest. */
+ * kernel (EINVAL for box staging while the tiles are short). */
 pflbm_status pflbm_batch_set_config(pflbm_batch* b, int mode, int ctas_per_sm);
+
+/* Tile shape of the batch: 32 x 16 tiles (rows = 16, the default; two
+ * collision nodes per thread) or 32 x 8 tiles (rows = 8; one node per
+ * thread, gather staging only, EINVAL with box staging).  Both compute the
+ * same step. */
+pflbm_status pflbm_batch_set_tile_rows(pflbm_batch* b, int rows);
+int pflbm_batch_get_tile_rows(const pflbm_batch* b);
+
+/* Time trial steps of every candidate (staging mode x tile rows x CTAs per
+ * SM) on the current states, which stay unchanged, and keep the fastest;
+ * the outputs (each may be NULL) receive the mode and CTAs per SM, and
+ * pflbm_batch_get_tile_rows the tile rows.  ESTATE before the first batch
+ * step. */
 pflbm_status pflbm_batch_autotune(pflbm_batch* b, int trial_steps, int* mode_out,
                                   int* ctas_per_sm_out);
 
-/* Work items (domain tiles) of one batch step. */
+/* Work items (domain tiles of the current shape) of one batch step. */
 long long pflbm_batch_items(const pflbm_batch* b);
 
 void pflbm_batch_destroy(pflbm_batch* b);

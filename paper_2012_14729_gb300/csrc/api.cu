@@ -988,9 +988,11 @@ struct pflbm_batch {
   pflbm_domain** doms;
   cudaStream_t stream;
   char* ws;
-  size_t table_off, items_off;
-  int nitems;
-  int mode, ctas_per_sm;
+  size_t table_off;
+  // work-lists for tiles of kTY rows ([0]) and of kShortRows rows ([1])
+  size_t items_off[2];
+  int nitems[2];
+  int mode, ctas_per_sm, rows;
   int graphs;
   cudaGraphExec_t gexec;
   StepArgs* host_table;  // staging of the argument table
@@ -1000,9 +1002,11 @@ namespace {
 
 constexpr int kBatchGraphSteps = 16;  // steps captured per batch graph (even)
 
-long long tiles_of(const pflbm_domain* d) {
-  return (long long)((d->nx + kTX - 1) / kTX) * ((d->ny + kTY - 1) / kTY);
+long long tiles_of(const pflbm_domain* d, int rows) {
+  return (long long)((d->nx + kTX - 1) / kTX) * ((d->ny + rows - 1) / rows);
 }
+int rows_slot(int rows) { return rows == kTY ? 0 : 1; }
+constexpr int kBatchRows[2] = {kTY, kShortRows};
 
 void batch_drop_graph(pflbm_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -1031,12 +1035,14 @@ cudaError_t upload_table(pflbm_batch* b, int keep_phiu, int firsts) {
 
 int batch_grid(const pflbm_batch* b) {
   const long long g = (long long)num_sms() * b->ctas_per_sm;
-  return (int)(g < b->nitems ? g : b->nitems);
+  const int n = b->nitems[rows_slot(b->rows)];
+  return (int)(g < n ? g : n);
 }
 
 cudaError_t batch_launch(const pflbm_batch* b, int bp) {
-  return launch_batch(b->mode, reinterpret_cast<const StepArgs*>(b->ws + b->table_off),
-                      reinterpret_cast<const int4*>(b->ws + b->items_off), b->nitems, bp,
+  const int r = rows_slot(b->rows);
+  return launch_batch(b->mode, b->rows, reinterpret_cast<const StepArgs*>(b->ws + b->table_off),
+                      reinterpret_cast<const int4*>(b->ws + b->items_off[r]), b->nitems[r], bp,
                       batch_grid(b), b->stream);
 }
 
@@ -1046,12 +1052,16 @@ extern "C" {
 
 size_t pflbm_batch_workspace_bytes(int n, pflbm_domain* const* doms) {
   if (n <= 0 || !doms) return 0;
-  long long items = 0;
-  for (int i = 0; i < n; ++i) {
-    if (!doms[i]) return 0;
-    items += tiles_of(doms[i]);
+  size_t bytes = align_up(sizeof(StepArgs) * 2 * (size_t)n);
+  for (int r = 0; r < 2; ++r) {
+    long long items = 0;
+    for (int i = 0; i < n; ++i) {
+      if (!doms[i]) return 0;
+      items += tiles_of(doms[i], kBatchRows[r]);
+    }
+    bytes += align_up(sizeof(int4) * (size_t)items);
   }
-  return align_up(sizeof(StepArgs) * 2 * (size_t)n) + align_up(sizeof(int4) * (size_t)items);
+  return bytes;
 }
 
 pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_workspace,
@@ -1089,34 +1099,41 @@ pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_work
   b->stream = (cudaStream_t)cuda_stream;
   b->ws = (char*)dev_workspace;
   b->table_off = 0;
-  b->items_off = align_up(sizeof(StepArgs) * 2 * (size_t)n);
   b->mode = kGather;
   b->ctas_per_sm = batch_blocks_per_sm(kGather);
-  // work-list sorted by force form, then by domain and tile (row-major)
-  long long items = 0;
-  for (int i = 0; i < n; ++i) items += tiles_of(doms[i]);
-  int4* h = new (std::nothrow) int4[items];
-  if (!h) {
-    pflbm_batch_destroy(b);
-    return PFLBM_EINVAL;
-  }
-  long long k = 0;
-  for (int form = 0; form < 8; ++form)
-    for (int i = 0; i < n; ++i) {
-      if (doms[i]->par.force != form) continue;
-      const int ntx = (doms[i]->nx + kTX - 1) / kTX, nty = (doms[i]->ny + kTY - 1) / kTY;
-      for (int ty = 0; ty < nty; ++ty)
-        for (int tx = 0; tx < ntx; ++tx) h[k++] = make_int4(i, tx * kTX, ty * kTY, form);
+  b->rows = kTY;
+  // one work-list per tile height, each sorted by force form, then by domain
+  // and tile (row-major)
+  size_t off = align_up(sizeof(StepArgs) * 2 * (size_t)n);
+  for (int r = 0; r < 2; ++r) {
+    const int rows = kBatchRows[r];
+    long long items = 0;
+    for (int i = 0; i < n; ++i) items += tiles_of(doms[i], rows);
+    int4* h = new (std::nothrow) int4[items];
+    if (!h) {
+      pflbm_batch_destroy(b);
+      return PFLBM_EINVAL;
     }
-  b->nitems = (int)k;
-  cudaError_t e = cudaMemcpyAsync(b->ws + b->items_off, h, sizeof(int4) * k,
-                                  cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  delete[] h;
-  if (e != cudaSuccess) {
-    set_err("pflbm_batch_create", e);
-    pflbm_batch_destroy(b);
-    return PFLBM_ECUDA;
+    long long k = 0;
+    for (int form = 0; form < 8; ++form)
+      for (int i = 0; i < n; ++i) {
+        if (doms[i]->par.force != form) continue;
+        const int ntx = (doms[i]->nx + kTX - 1) / kTX, nty = (doms[i]->ny + rows - 1) / rows;
+        for (int ty = 0; ty < nty; ++ty)
+          for (int tx = 0; tx < ntx; ++tx) h[k++] = make_int4(i, tx * kTX, ty * rows, form);
+      }
+    b->items_off[r] = off;
+    b->nitems[r] = (int)k;
+    off += align_up(sizeof(int4) * (size_t)k);
+    cudaError_t e = cudaMemcpyAsync(b->ws + b->items_off[r], h, sizeof(int4) * k,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    delete[] h;
+    if (e != cudaSuccess) {
+      set_err("pflbm_batch_create", e);
+      pflbm_batch_destroy(b);
+      return PFLBM_ECUDA;
+    }
   }
   *out = b;
   return PFLBM_OK;
@@ -1137,13 +1154,32 @@ pflbm_status pflbm_batch_set_config(pflbm_batch* b, int mode, int ctas_per_sm) {
   if (!b || mode < 0 || mode >= kNumModes || ctas_per_sm < 1 ||
       ctas_per_sm > batch_blocks_per_sm(mode))
     return PFLBM_EINVAL;
+  if (mode == kBoxes && b->rows != kTY) {
+    set_msg("pflbm_batch_set_config: box staging needs tiles of the full height");
+    return PFLBM_EINVAL;
+  }
   b->mode = mode;
   b->ctas_per_sm = ctas_per_sm;
   batch_drop_graph(b);
   return PFLBM_OK;
 }
 
-long long pflbm_batch_items(const pflbm_batch* b) { return b ? b->nitems : -1; }
+pflbm_status pflbm_batch_set_tile_rows(pflbm_batch* b, int rows) {
+  if (!b || (rows != kTY && rows != kShortRows)) return PFLBM_EINVAL;
+  if (rows != kTY && b->mode == kBoxes) {
+    set_msg("pflbm_batch_set_tile_rows: box staging needs tiles of the full height");
+    return PFLBM_EINVAL;
+  }
+  b->rows = rows;
+  batch_drop_graph(b);
+  return PFLBM_OK;
+}
+
+int pflbm_batch_get_tile_rows(const pflbm_batch* b) { return b ? b->rows : -1; }
+
+long long pflbm_batch_items(const pflbm_batch* b) {
+  return b ? b->nitems[rows_slot(b->rows)] : -1;
+}
 
 pflbm_status pflbm_batch_step(pflbm_batch* b, int nsteps) {
   if (!b || nsteps < 0) return PFLBM_EINVAL;
@@ -1222,24 +1258,31 @@ pflbm_status pflbm_batch_autotune(pflbm_batch* b, int trial_steps, int* mode_out
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int keep_mode = b->mode, keep_cps = b->ctas_per_sm;
+  const int keep_mode = b->mode, keep_cps = b->ctas_per_sm, keep_rows = b->rows;
   float best = 1e30f;
-  int best_mode = keep_mode, best_cps = keep_cps;
+  int best_mode = keep_mode, best_cps = keep_cps, best_rows = keep_rows;
+  // candidates: staging mode x tile rows (short tiles with gathers only) x
+  // persistent CTAs per SM
   for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
-    for (int cps = 1; cps <= batch_blocks_per_sm(m) && e == cudaSuccess; ++cps) {
-      b->mode = m;
-      b->ctas_per_sm = cps;
-      e = batch_launch(b, 0);  // warm-up
-      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-      for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = batch_launch(b, 0);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e == cudaSuccess && ms < best) {
-        best = ms;
-        best_mode = m;
-        best_cps = cps;
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+      if (m == kBoxes && kBatchRows[r] != kTY) continue;
+      for (int cps = 1; cps <= batch_blocks_per_sm(m) && e == cudaSuccess; ++cps) {
+        b->mode = m;
+        b->rows = kBatchRows[r];
+        b->ctas_per_sm = cps;
+        e = batch_launch(b, 0);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = batch_launch(b, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          best_mode = m;
+          best_cps = cps;
+          best_rows = kBatchRows[r];
+        }
       }
     }
   }
@@ -1247,6 +1290,7 @@ pflbm_status pflbm_batch_autotune(pflbm_batch* b, int trial_steps, int* mode_out
   if (e1) cudaEventDestroy(e1);
   b->mode = e == cudaSuccess ? best_mode : keep_mode;
   b->ctas_per_sm = e == cudaSuccess ? best_cps : keep_cps;
+  b->rows = e == cudaSuccess ? best_rows : keep_rows;
   batch_drop_graph(b);
   if (e != cudaSuccess) {
     set_err("pflbm_batch_autotune", e);

@@ -2,7 +2,9 @@
 // advance together, one persistent launch per time step.  The CTAs walk a
 // work-list of (instance, tile) items sorted by force form; each item runs
 // the same per-tile passes as the single-domain kernels, with the instance's
-// arguments taken from a table in global memory (FP32 storage).
+// arguments taken from a table in global memory (FP32 storage).  Gather-mode
+// batches run tiles of kTY or kShortRows rows (two or one collision nodes
+// per thread); the autotuner times both.
 #include "step_kernel.cuh"
 
 namespace pflbm {
@@ -18,26 +20,28 @@ constexpr int kFieldsMax =
               cmax(Fields<kCSF1>::BYTES, Fields<kCSF2>::BYTES)));
 constexpr int kArgsBytes = pad128((int)sizeof(StepArgs));
 
-template <class ST, int NT, bool INNER>
+template <class ST, int NT, bool INNER, int TY>
 __device__ __forceinline__ void gather_item(const StepArgs& a, int form, unsigned char* fs, int x0,
                                             int y0) {
-  const GatherSrc<ST, INNER> src{};
+  using S = GatherSrc<ST, INNER>;
+  const S src{};
   switch (form) {
-    case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
-    case kSTF2: step_tile<kSTF2, ST, NT>(a, src, fs, x0, y0); break;
-    case kCPF1: step_tile<kCPF1, ST, NT>(a, src, fs, x0, y0); break;
-    case kCPF2: step_tile<kCPF2, ST, NT>(a, src, fs, x0, y0); break;
-    case kPF1: step_tile<kPF1, ST, NT>(a, src, fs, x0, y0); break;
-    case kPF2: step_tile<kPF2, ST, NT>(a, src, fs, x0, y0); break;
-    case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
-    default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
+    case kSTF1: step_tile<kSTF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kSTF2: step_tile<kSTF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kCPF1: step_tile<kCPF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kCPF2: step_tile<kCPF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kPF1: step_tile<kPF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kPF2: step_tile<kPF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kCSF1: step_tile<kCSF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    default: step_tile<kCSF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
   }
 }
 
-template <class ST, int MODE, int NT>
+template <class ST, int MODE, int NT, int TY>
 __device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, int form,
                                          unsigned char* bx, unsigned char* fs, int x0, int y0) {
   if constexpr (MODE == kBoxes) {
+    static_assert(TY == kTY, "box staging is laid out for full tiles");
     const BoxSrc<ST> src{bx};
     switch (form) {
       case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
@@ -49,10 +53,10 @@ __device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, 
       case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
       default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
     }
-  } else if (inner_tile(a.L, x0, y0)) {
-    gather_item<ST, NT, true>(a, form, fs, x0, y0);
+  } else if (inner_tile<TY>(a.L, x0, y0)) {
+    gather_item<ST, NT, true, TY>(a, form, fs, x0, y0);
   } else {
-    gather_item<ST, NT, false>(a, form, fs, x0, y0);
+    gather_item<ST, NT, false, TY>(a, form, fs, x0, y0);
   }
 }
 
@@ -72,7 +76,7 @@ struct BatchCfg<kGather> {
   static constexpr int NT = kThreadsGather, MINB = kBlocksGather;
 };
 
-template <class ST, int MODE>
+template <class ST, int MODE, int TY>
 __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
     k_step_batch(const StepArgs* __restrict__ table, const int4* __restrict__ items, int nitems,
                  int bp) {
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
         __syncthreads();
       }
     }
-    run_item<ST, MODE, NT>(a, ga, item.w, bx, fs, x0, y0);
+    run_item<ST, MODE, NT, TY>(a, ga, item.w, bx, fs, x0, y0);
   }
 }
 
@@ -125,18 +129,18 @@ constexpr int batch_smem() {
   return kArgsBytes + 128 + (MODE == kBoxes ? Boxes<StoreF32>::BYTES : 0) + kFieldsMax;
 }
 
-template <int MODE>
+template <int MODE, int TY>
 cudaError_t launch_batch_mode(const StepArgs* table, const int4* items, int nitems, int bp,
                               int grid, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_batch<StoreF32, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_batch<StoreF32, MODE, TY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          batch_smem<MODE>());
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_step_batch<StoreF32, MODE><<<grid, BatchCfg<MODE>::NT, batch_smem<MODE>(), s>>>(
+  k_step_batch<StoreF32, MODE, TY><<<grid, BatchCfg<MODE>::NT, batch_smem<MODE>(), s>>>(
       table, items, nitems, bp);
   return cudaGetLastError();
 }
@@ -147,10 +151,16 @@ int batch_blocks_per_sm(int mode) {
   return mode == kBoxes ? BatchCfg<kBoxes>::MINB : BatchCfg<kGather>::MINB;
 }
 
-cudaError_t launch_batch(int mode, const StepArgs* table, const int4* items, int nitems, int bp,
-                         int grid, cudaStream_t s) {
-  if (mode == kBoxes) return launch_batch_mode<kBoxes>(table, items, nitems, bp, grid, s);
-  return launch_batch_mode<kGather>(table, items, nitems, bp, grid, s);
+cudaError_t launch_batch(int mode, int rows, const StepArgs* table, const int4* items,
+                         int nitems, int bp, int grid, cudaStream_t s) {
+  if (mode == kBoxes) {
+    if (rows != kTY) return cudaErrorInvalidValue;
+    return launch_batch_mode<kBoxes, kTY>(table, items, nitems, bp, grid, s);
+  }
+  if (rows == kShortRows)
+    return launch_batch_mode<kGather, kShortRows>(table, items, nitems, bp, grid, s);
+  if (rows != kTY) return cudaErrorInvalidValue;
+  return launch_batch_mode<kGather, kTY>(table, items, nitems, bp, grid, s);
 }
 
 }  // namespace pflbm

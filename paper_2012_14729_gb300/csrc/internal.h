@@ -80,6 +80,9 @@ enum TapePlane {
 // Tile of the fused step kernel.
 constexpr int kTX = 32;
 constexpr int kTY = 16;
+// Rows of the short tiles a gather-mode batch may run instead (one collision
+// node per thread of a 256-thread CTA).
+constexpr int kShortRows = 8;
 // How a tile gets the populations it pulls (the autotuner picks per domain):
 //   kBoxes   TMA box loads into shared memory (cp.async for seam tiles); a
 //            persistent grid of two 512-thread CTAs per SM, each walking tiles
@@ -139,11 +142,12 @@ cudaError_t launch_adjoint_init(const AdjArgs& A, const float* phi0, float* dphi
 
 // Batched step over a work-list (batch.cu): table holds 2 StepArgs per
 // instance (entry 2 i + p reads buffer cur_i ^ p), items (instance, x0, y0,
-// form); `bp` is the step parity; `grid` persistent CTAs.
+// form) for tiles of `rows` rows (kTY, or kShortRows in the gather mode);
+// `bp` is the step parity; `grid` persistent CTAs.
 int batch_blocks_per_sm(int mode);
 int num_sms();  // streaming multiprocessors of the current device
-cudaError_t launch_batch(int mode, const StepArgs* table, const int4* items, int nitems, int bp,
-                         int grid, cudaStream_t s);
+cudaError_t launch_batch(int mode, int rows, const StepArgs* table, const int4* items,
+                         int nitems, int bp, int grid, cudaStream_t s);
 
 cudaError_t launch_step_fp32(int form, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp16(int form, int mode, const StepArgs& a, cudaStream_t s);

@@ -96,11 +96,12 @@ __host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; 
 // ---------------------------------------------------------------------------
 // shared-memory geometry: per-tile fields, and the box set of kBoxes
 // ---------------------------------------------------------------------------
-template <int FORM, bool TAPE = false>
+// TY: rows of the tile (kTY, or fewer for the batch's short tiles)
+template <int FORM, bool TAPE = false, int TY = kTY>
 struct Fields {
-  static constexpr int B3X = kTX + 6, B3Y = kTY + 6;  // tile + 3 ring
-  static constexpr int B2X = kTX + 4, B2Y = kTY + 4;  // tile + 2 ring
-  static constexpr int B1X = kTX + 2, B1Y = kTY + 2;  // tile + 1 ring
+  static constexpr int B3X = kTX + 6, B3Y = TY + 6;  // tile + 3 ring
+  static constexpr int B2X = kTX + 4, B2Y = TY + 4;  // tile + 2 ring
+  static constexpr int B1X = kTX + 2, B1Y = TY + 2;  // tile + 1 ring
   static constexpr int N3 = B3X * B3Y, N2 = B2X * B2Y, N1 = B1X * B1Y;
   static constexpr int NE = extra_fields<FORM>();
   // lap phi is kept past pass 2 only by the forms whose force uses it (and
@@ -254,9 +255,10 @@ struct GatherSrc {
 // ---------------------------------------------------------------------------
 // box staging
 // ---------------------------------------------------------------------------
-// Tiles whose 3-ring and its pull sources lie inside the domain.
+// Tiles (of TY rows) whose 3-ring and its pull sources lie inside the domain.
+template <int TY = kTY>
 __device__ __forceinline__ bool inner_tile(const Lattice& L, int x0, int y0) {
-  return x0 >= 4 && x0 + kTX + 4 <= L.nx && y0 >= 4 && y0 + kTY + 4 <= L.ny;
+  return x0 >= 4 && x0 + kTX + 4 <= L.nx && y0 >= 4 && y0 + TY + 4 <= L.ny;
 }
 
 // Tiles whose 18 boxes lie inside the stored planes without wrapping.
@@ -408,14 +410,14 @@ __device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, f
 // ---------------------------------------------------------------------------
 // TAPE: also record, per interior node, the step's intermediates that the
 // adjoint reads (plane layout of the TapePlane enum, a.tape + plane * nx ny).
-template <int FORM, class ST, int NT, class SRC, bool TAPE = false>
+template <int FORM, class ST, int NT, class SRC, bool TAPE = false, int TY = kTY>
 __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, unsigned char* fs,
                                           int x0, int y0) {
-  using F = Fields<FORM, TAPE>;
+  using F = Fields<FORM, TAPE, TY>;
   constexpr int B3X = F::B3X, B2X = F::B2X, B1X = F::B1X, B1Y = F::B1Y;
   constexpr int N2 = F::N2, N1 = F::N1;
-  constexpr int NPT = kTX * kTY / NT;  // collision nodes per thread
-  static_assert(kTX * kTY % NT == 0, "whole collision nodes per thread");
+  constexpr int NPT = kTX * TY / NT;  // collision nodes per thread
+  static_assert(kTX * TY % NT == 0, "whole collision nodes per thread");
   // level-1 field slots in s2, ring-1 slots in s1
   constexpr int GX = 0, GY = 1, MU = 2, LAP = 3, E0 = F::kLap ? 4 : 3;
   constexpr int FX = 0, FY = 1, UX = 2, UY = 3, PUX = 4, PUY = 5;
@@ -455,7 +457,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
                   : src.phi(a, r, cc, col(x0 - 3 + cc), L.wall ? yn : wrap(yn, L.ny));
   }
   __syncthreads();
-  if (!kIn && L.wall && (y0 - 3 < 0 || y0 + kTY + 3 > L.ny)) {
+  if (!kIn && L.wall && (y0 - 3 < 0 || y0 + TY + 3 > L.ny)) {
     // mirror ghosts of phi about the wall planes
     for (int k = tid; k < F::N3; k += NT) {
       const int r = k / B3X, cc = k - r * B3X;
@@ -574,7 +576,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     s1[PUY * N1 + k] = phi * uy;
     if constexpr (TAPE) {
       const int gxn = x0 - 1 + lx, gyn = y0 - 1 + ly;
-      if (lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY && gxn < L.nx && gyn < L.ny) {
+      if (lx >= 1 && lx <= kTX && ly >= 1 && ly <= TY && gxn < L.nx && gyn < L.ny) {
         float* t = a.tape + gyn * L.nx + gxn;
         t[TP_A0 * nn] = a0;
         t[TP_A1 * nn] = a1;

@@ -101,6 +101,8 @@ SIGNATURES = {
     "pflbm_batch_step": (_i, [_vp, _i]),
     "pflbm_batch_set_graphs": (_i, [_vp, _i]),
     "pflbm_batch_set_config": (_i, [_vp, _i, _i]),
+    "pflbm_batch_set_tile_rows": (_i, [_vp, _i]),
+    "pflbm_batch_get_tile_rows": (_i, [_vp]),
     "pflbm_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pflbm_batch_items": (ctypes.c_longlong, [_vp]),
     "pflbm_batch_destroy": (None, [_vp]),
@@ -310,6 +312,14 @@ def pflbm_batch_create(handles, workspace_ptr, ws_bytes, stream_ptr):
     return b
 
 
+def pflbm_batch_set_tile_rows(b, rows: int):
+    _check(load().pflbm_batch_set_tile_rows(b, int(rows)), "pflbm_batch_set_tile_rows")
+
+
+def pflbm_batch_get_tile_rows(b) -> int:
+    return int(load().pflbm_batch_get_tile_rows(b))
+
+
 def pflbm_batch_step(b, nsteps: int):
     _check(load().pflbm_batch_step(b, int(nsteps)), "pflbm_batch_step")
 
@@ -371,13 +381,25 @@ class Batch:
         pflbm_batch_set_graphs(self.h, enable)
         return self
 
-    def config(self, mode, ctas_per_sm: int) -> "Batch":
-        pflbm_batch_set_config(self.h, STAGE_MODES.get(mode, mode), ctas_per_sm)
+    def config(self, mode, ctas_per_sm: int, rows: int = 16) -> "Batch":
+        """Staging mode, CTAs per SM and tile rows (16, or 8 with gathers)."""
+        mode = STAGE_MODES.get(mode, mode)
+        if rows == 16:  # full tiles first: every mode accepts them
+            pflbm_batch_set_tile_rows(self.h, 16)
+            pflbm_batch_set_config(self.h, mode, ctas_per_sm)
+        else:
+            pflbm_batch_set_config(self.h, mode, ctas_per_sm)
+            pflbm_batch_set_tile_rows(self.h, rows)
         return self
 
+    @property
+    def tile_rows(self) -> int:
+        return pflbm_batch_get_tile_rows(self.h)
+
     def autotune(self, trial_steps: int = 5):
+        """(mode, CTAs per SM, tile rows) of the fastest candidate, now set."""
         m, c = pflbm_batch_autotune(self.h, trial_steps)
-        return {v: k for k, v in STAGE_MODES.items()}[m], c
+        return {v: k for k, v in STAGE_MODES.items()}[m], c, self.tile_rows
 
     def synchronize(self):
         self.stream.synchronize()

@@ -71,16 +71,31 @@ def test_batch_equals_individual_steps(pf):
     _assert_close(_pops(doms), _pops(solo))
 
 
-@pytest.mark.parametrize("mode,cps", [("boxes", 2), ("boxes", 1), ("gather", 3), ("gather", 1)])
-def test_batch_configs_agree(pf, mode, cps):
+@pytest.mark.parametrize("mode,cps,rows", [("boxes", 2, 16), ("boxes", 1, 16), ("gather", 3, 16),
+                                           ("gather", 1, 16), ("gather", 4, 8), ("gather", 2, 8)])
+def test_batch_configs_agree(pf, mode, cps, rows):
     insts = _instances()
     ref = _domains(pf, insts)
     pf.Batch(ref).step(12).synchronize()
     doms = _domains(pf, insts)
-    b = pf.Batch(doms).config(mode, cps)
+    b = pf.Batch(doms).config(mode, cps, rows)
+    assert b.tile_rows == rows
+    assert b.items == sum(((nx + 31) // 32) * ((ny + rows - 1) // rows)
+                          for nx, ny, *_ in insts)
     b.step(12)
     b.synchronize()
     _assert_close(_pops(doms), _pops(ref))
+
+
+def test_batch_short_tiles_refuse_boxes(pf):
+    doms = _domains(pf, _instances())
+    b = pf.Batch(doms).config("gather", 4, 8)
+    with pytest.raises(pf.PflbmError):
+        pf.pflbm_batch_set_config(b.h, pf.STAGE_MODES["boxes"], 2)
+    with pytest.raises(pf.PflbmError):
+        pf.pflbm_batch_set_tile_rows(b.h, 12)
+    b.config("boxes", 2)  # full tiles again, then boxes
+    assert b.tile_rows == 16
 
 
 def test_batch_graphs_equal_plain(pf):
@@ -117,8 +132,9 @@ def test_batch_autotune_keeps_state(pf):
     b.step(3)
     b.synchronize()
     before = _pops(doms)
-    mode, cps = b.autotune(2)
-    assert mode in ("boxes", "gather") and cps >= 1
+    mode, cps, rows = b.autotune(2)
+    assert mode in ("boxes", "gather") and cps >= 1 and rows in (8, 16)
+    assert rows == 16 or mode == "gather"
     after = _pops(doms)
     for x, y in zip(before, after):
         np.testing.assert_array_equal(x[0], y[0])
