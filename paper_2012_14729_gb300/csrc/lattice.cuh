@@ -40,11 +40,17 @@ __host__ __device__ constexpr int extra_fields() {
 // ---------------------------------------------------------------------------
 // storage formats
 // ---------------------------------------------------------------------------
+// 16-bit formats store p_i 2^s / w_i (h_0 in float32).  dec/enc convert to
+// and from the population value; raw/enc_raw only change the type, for the
+// step kernel, which computes in that storage scale (the weights and 2^s then
+// sit in its per-node constants).
 struct StoreF32 {
   static constexpr bool kSplitH0 = false;
   using T = float;
   __device__ static __forceinline__ float dec(T v, float w_inv_scale) { return v; }
   __device__ static __forceinline__ T enc(float v, float scale_over_w) { return v; }
+  __device__ static __forceinline__ float raw(T v) { return v; }
+  __device__ static __forceinline__ T enc_raw(float v) { return v; }
 };
 struct StoreF16 {
   static constexpr bool kSplitH0 = true;
@@ -55,6 +61,8 @@ struct StoreF16 {
   __device__ static __forceinline__ T enc(float v, float scale_over_w) {
     return __float2half_rn(v * scale_over_w);
   }
+  __device__ static __forceinline__ float raw(T v) { return __half2float(v); }
+  __device__ static __forceinline__ T enc_raw(float v) { return __float2half_rn(v); }
 };
 struct StoreBF16 {
   static constexpr bool kSplitH0 = true;
@@ -65,6 +73,8 @@ struct StoreBF16 {
   __device__ static __forceinline__ T enc(float v, float scale_over_w) {
     return __float2bfloat16_rn(v * scale_over_w);
   }
+  __device__ static __forceinline__ float raw(T v) { return __bfloat162float(v); }
+  __device__ static __forceinline__ T enc_raw(float v) { return __float2bfloat16_rn(v); }
 };
 
 // f_i, population i at storage index idx
@@ -108,6 +118,81 @@ __device__ __forceinline__ void store_h(const StepArgs& a, int idx, float v) {
   } else {
     T* base = reinterpret_cast<T*>(a.h_out) + (size_t)I * a.L.plane;
     base[idx] = v;
+  }
+}
+
+// The same in the storage scale of the format (the step kernel's arithmetic).
+template <class ST, int I>
+__device__ __forceinline__ float load_fs(const StepArgs& a, int idx) {
+  using T = typename ST::T;
+  const T* base = reinterpret_cast<const T*>(a.f_in) + (size_t)I * a.L.plane;
+  return ST::raw(__ldg(base + idx));
+}
+template <class ST, int I>
+__device__ __forceinline__ float load_hs(const StepArgs& a, int idx) {
+  using T = typename ST::T;
+  if constexpr (ST::kSplitH0 && I == 0) return __ldg(a.h0_in + idx);
+  const int pl = ST::kSplitH0 ? I - 1 : I;
+  const T* base = reinterpret_cast<const T*>(a.h_in) + (size_t)pl * a.L.plane;
+  return ST::raw(__ldg(base + idx));
+}
+template <class ST, int I>
+__device__ __forceinline__ void store_fs(const StepArgs& a, int idx, float v) {
+  using T = typename ST::T;
+  T* base = reinterpret_cast<T*>(a.f_out) + (size_t)I * a.L.plane;
+  base[idx] = ST::enc_raw(v);
+}
+template <class ST, int I>
+__device__ __forceinline__ void store_hs(const StepArgs& a, int idx, float v) {
+  using T = typename ST::T;
+  if constexpr (ST::kSplitH0 && I == 0) {
+    a.h0_out[idx] = v;
+  } else {
+    const int pl = ST::kSplitH0 ? I - 1 : I;
+    T* base = reinterpret_cast<T*>(a.h_out) + (size_t)pl * a.L.plane;
+    base[idx] = ST::enc_raw(v);
+  }
+}
+
+// Moments of populations in storage scale (h_0 and FP32 values as is):
+// phi = sum h_i, sum f_i and j = sum c_i f_i.  FP32 sums in direction order;
+// the 16-bit scale groups the directions of one weight class.
+template <class ST>
+__device__ __forceinline__ float phi_sum(const float* h, const Phys& P) {
+  if constexpr (ST::kSplitH0) {
+    const float ax = (h[1] + h[2]) + (h[3] + h[4]), dg = (h[5] + h[6]) + (h[7] + h[8]);
+    return h[0] + fmaf(qw(1) * P.inv_sh, ax, (qw(5) * P.inv_sh) * dg);
+  } else {
+    float t = h[0];
+    t += h[1];
+    t += h[2];
+    t += h[3];
+    t += h[4];
+    t += h[5];
+    t += h[6];
+    t += h[7];
+    t += h[8];
+    return t;
+  }
+}
+template <class ST>
+__device__ __forceinline__ float f_sum(const float* f, const Phys& P) {
+  if constexpr (ST::kSplitH0) {
+    const float ax = (f[1] + f[2]) + (f[3] + f[4]), dg = (f[5] + f[6]) + (f[7] + f[8]);
+    return fmaf(qw(0) * P.inv_sf, f[0], fmaf(qw(1) * P.inv_sf, ax, (qw(5) * P.inv_sf) * dg));
+  } else {
+    return f[0] + (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+  }
+}
+template <class ST>
+__device__ __forceinline__ void f_flux(const float* f, const Phys& P, float& jx, float& jy) {
+  if constexpr (ST::kSplitH0) {
+    const float ca = qw(1) * P.inv_sf, cd = qw(5) * P.inv_sf;
+    jx = fmaf(ca, f[1] - f[3], cd * ((f[5] - f[6]) + (f[8] - f[7])));
+    jy = fmaf(ca, f[2] - f[4], cd * ((f[5] - f[8]) + (f[6] - f[7])));
+  } else {
+    jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    jy = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
   }
 }
 
@@ -193,6 +278,38 @@ __device__ __forceinline__ Pull pull_idx_inner(const Lattice& L, int x, int y) {
   p.i[7] = rm + 1;
   p.i[8] = rm - 1;
   return p;
+}
+
+// pulled populations in storage scale, and phi from them
+template <class ST>
+__device__ __forceinline__ void pull_hs(const StepArgs& a, const Pull& q, float* h) {
+  h[0] = load_hs<ST, 0>(a, q.i[0]);
+  h[1] = load_hs<ST, 1>(a, q.i[1]);
+  h[2] = load_hs<ST, 2>(a, q.i[2]);
+  h[3] = load_hs<ST, 3>(a, q.i[3]);
+  h[4] = load_hs<ST, 4>(a, q.i[4]);
+  h[5] = load_hs<ST, 5>(a, q.i[5]);
+  h[6] = load_hs<ST, 6>(a, q.i[6]);
+  h[7] = load_hs<ST, 7>(a, q.i[7]);
+  h[8] = load_hs<ST, 8>(a, q.i[8]);
+}
+template <class ST>
+__device__ __forceinline__ void pull_fs(const StepArgs& a, const Pull& q, float* f) {
+  f[0] = load_fs<ST, 0>(a, q.i[0]);
+  f[1] = load_fs<ST, 1>(a, q.i[1]);
+  f[2] = load_fs<ST, 2>(a, q.i[2]);
+  f[3] = load_fs<ST, 3>(a, q.i[3]);
+  f[4] = load_fs<ST, 4>(a, q.i[4]);
+  f[5] = load_fs<ST, 5>(a, q.i[5]);
+  f[6] = load_fs<ST, 6>(a, q.i[6]);
+  f[7] = load_fs<ST, 7>(a, q.i[7]);
+  f[8] = load_fs<ST, 8>(a, q.i[8]);
+}
+template <class ST>
+__device__ __forceinline__ float pull_phi_s(const StepArgs& a, const Pull& q) {
+  float h[9];
+  pull_hs<ST>(a, q, h);
+  return phi_sum<ST>(h, a.p);
 }
 
 template <class ST>

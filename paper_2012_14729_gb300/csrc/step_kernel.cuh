@@ -143,35 +143,33 @@ struct BoxSrc {
   static constexpr bool kInner = false, kWallX = false;
   using G = Boxes<ST>;
   const unsigned char* bx;
+  // populations in the storage scale of the format
   template <int I>
-  __device__ __forceinline__ float h(int r, int c, const Phys& P) const {
+  __device__ __forceinline__ float h(int r, int c, const Phys&) const {
     if constexpr (ST::kSplitH0 && I == 0) {
       return reinterpret_cast<const float*>(bx + G::h_off(0))[r * G::PW + c];
     } else {
-      const typename ST::T v =
-          reinterpret_cast<const typename ST::T*>(bx + G::h_off(I))[r * G::PW + c];
-      return ST::dec(v, qw(I) * P.inv_sh);
+      return ST::raw(reinterpret_cast<const typename ST::T*>(bx + G::h_off(I))[r * G::PW + c]);
     }
   }
   template <int I>
-  __device__ __forceinline__ float f(int r, int c, const Phys& P) const {
-    const typename ST::T v =
-        reinterpret_cast<const typename ST::T*>(bx + G::f_off(I))[r * G::PW + c];
-    return ST::dec(v, qw(I) * P.inv_sf);
+  __device__ __forceinline__ float f(int r, int c, const Phys&) const {
+    return ST::raw(reinterpret_cast<const typename ST::T*>(bx + G::f_off(I))[r * G::PW + c]);
   }
   __device__ __forceinline__ float phi(const StepArgs& a, int r, int cc, int, int) const {
     const int c = cc + G::XPAD - 3;
     const Phys& P = a.p;
-    float s = h<0>(r, c, P);
-    s += h<1>(r, c - 1, P);
-    s += h<2>(r, c, P);
-    s += h<3>(r, c + 1, P);
-    s += h<4>(r, c, P);
-    s += h<5>(r, c - 1, P);
-    s += h<6>(r, c + 1, P);
-    s += h<7>(r, c + 1, P);
-    s += h<8>(r, c - 1, P);
-    return s;
+    float hh[9];
+    hh[0] = h<0>(r, c, P);
+    hh[1] = h<1>(r, c - 1, P);
+    hh[2] = h<2>(r, c, P);
+    hh[3] = h<3>(r, c + 1, P);
+    hh[4] = h<4>(r, c, P);
+    hh[5] = h<5>(r, c - 1, P);
+    hh[6] = h<6>(r, c + 1, P);
+    hh[7] = h<7>(r, c + 1, P);
+    hh[8] = h<8>(r, c - 1, P);
+    return phi_sum<ST>(hh, P);
   }
   __device__ __forceinline__ void f_ring1(const StepArgs& a, int ly, int lx, int, int,
                                           float* f) const {
@@ -227,28 +225,29 @@ struct GatherSrc {
     if constexpr (INNER) return pull_idx_inner(L, gx, gy);
     else return pull_idx<XW>(L, gx, gy);
   }
+  // populations in the storage scale of the format
   __device__ __forceinline__ float phi(const StepArgs& a, int, int, int gx, int gy) const {
-    return pull_phi<ST>(a, idx(a.L, gx, gy));
+    return pull_phi_s<ST>(a, idx(a.L, gx, gy));
   }
   __device__ __forceinline__ void f_ring1(const StepArgs& a, int, int, int gx, int gy,
                                           float* f) const {
     const Pull q = idx(a.L, gx, gy);
-    f[1] = load_f<ST, 1>(a, q.i[1]);
-    f[2] = load_f<ST, 2>(a, q.i[2]);
-    f[3] = load_f<ST, 3>(a, q.i[3]);
-    f[4] = load_f<ST, 4>(a, q.i[4]);
-    f[5] = load_f<ST, 5>(a, q.i[5]);
-    f[6] = load_f<ST, 6>(a, q.i[6]);
-    f[7] = load_f<ST, 7>(a, q.i[7]);
-    f[8] = load_f<ST, 8>(a, q.i[8]);
+    f[1] = load_fs<ST, 1>(a, q.i[1]);
+    f[2] = load_fs<ST, 2>(a, q.i[2]);
+    f[3] = load_fs<ST, 3>(a, q.i[3]);
+    f[4] = load_fs<ST, 4>(a, q.i[4]);
+    f[5] = load_fs<ST, 5>(a, q.i[5]);
+    f[6] = load_fs<ST, 6>(a, q.i[6]);
+    f[7] = load_fs<ST, 7>(a, q.i[7]);
+    f[8] = load_fs<ST, 8>(a, q.i[8]);
   }
   __device__ __forceinline__ void f_node(const StepArgs& a, int, int, int gx, int gy,
                                          float* f) const {
-    pull_f<ST>(a, idx(a.L, gx, gy), f);
+    pull_fs<ST>(a, idx(a.L, gx, gy), f);
   }
   __device__ __forceinline__ void h_node(const StepArgs& a, int, int, int gx, int gy,
                                          float* h) const {
-    pull_h<ST>(a, idx(a.L, gx, gy), h);
+    pull_hs<ST>(a, idx(a.L, gx, gy), h);
   }
 };
 
@@ -430,6 +429,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   const int nn = L.nx * L.ny;
   constexpr bool kIn = SRC::kInner;
   constexpr bool kXw = SRC::kWallX;  // free-slip side walls (mirror columns)
+  // 16-bit formats: populations stay in their storage scale p_i 2^s / w_i
+  // (h_0 excepted); moments and collision constants carry the weights
+  constexpr bool kScaled = ST::kSplitH0;
   const auto col = [&](int x) { return kXw ? map_col(x, L.nx, 1) : wrap(x, L.nx); };
 
   // (phi u)^{t-1} of this thread's collision nodes, loaded first so that the
@@ -562,8 +564,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const float rho = P.rho_mid + P.drho_half * phi;
     Fx += (rho - P.rho0) * P.gx;
     Fy += (rho - P.rho0) * P.gy;
-    const float jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-    const float jy = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
+    float jx, jy;
+    f_flux<ST>(f, P, jx, jy);
     // Eq. mac: u = [sum c f + cs^2 F / 2] / (cs^2 rho)
     const float irho = __fdividef(1.0f, rho);
     const float ux = (3.0f * jx + 0.5f * Fx) * irho;
@@ -667,7 +669,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
 
     float f[9];
     src.f_node(a, ly, lx, gx, gy, f);
-    const float sumf = f[0] + (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+    const float sumf = f_sum<ST>(f, P);
     // Eq. mac: P = sum f + cs^2/2 u . grad rho
     const float Pr = sumf + (ux * drx + uy * dry) * (1.0f / 6.0f);
     // div(phi u) by Eq. ICS-1st on the ring-1 values
@@ -751,14 +753,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       const float hp = 3.0f * P.inv_tau_h * phi, hd = 3.0f * P.hforce;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
+        // weight of the class (float32), or the storage scale 2^s, which
+        // replaces w / w in the 16-bit scale p_i 2^s / w_i
         constexpr float wa = qw(1), wd = qw(5);
-        const float w = c == 0 ? wa : wd;
-        K.t1[c] = w * oP;
-        K.t2[c] = w * oR;
-        K.t3[c] = w * cff;
-        K.hc[c] = w * hb;
-        K.hu[c] = w * hp;
-        K.hd[c] = w * hd;
+        const float wf = kScaled ? P.sf : (c == 0 ? wa : wd);
+        const float wh = kScaled ? P.sh : (c == 0 ? wa : wd);
+        K.t1[c] = wf * oP;
+        K.t2[c] = wf * oR;
+        K.t3[c] = wf * cff;
+        K.hc[c] = wh * hb;
+        K.hu[c] = wh * hp;
+        K.hd[c] = wh * hd;
       }
     }
 
@@ -766,10 +771,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     {
       // rest population: s_0 = -1.5 |u|^2, c_0 = 0, wbar_0 = w_0 - 1
       constexpr float w0 = qw(0);
+      const float wf0 = kScaled ? P.sf : w0;
       const float s0 = -K.uu15;
       const float a0 = -K.uF, b0 = -K.uF - K.uR;
       fo[0] = fmaf(K.omf1, f[0],
-                   w0 * (fmaf(omf, Pr, cff * a0) + s0 * fmaf(omf, rho * (1.0f / 3.0f), cff * b0)));
+                   wf0 * (fmaf(omf, Pr, cff * a0) + s0 * fmaf(omf, rho * (1.0f / 3.0f), cff * b0)));
       const float heq0 = phi + (w0 - 1.0f) * emu;
       ho[0] = fmaf(K.omh1, h[0], fmaf(P.inv_tau_h, heq0, P.hforce * ((w0 - 1.0f) * A)));
     }
@@ -779,15 +785,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     collide_pair<6>(K, f[6], f[8], h[6], h[8], fo[6], fo[8], ho[6], ho[8]);
 
     const int o = (gy + 1) * L.nx + gx;
-    store_f<ST, 0>(a, o, fo[0]); store_h<ST, 0>(a, o, ho[0]);
-    store_f<ST, 1>(a, o, fo[1]); store_h<ST, 1>(a, o, ho[1]);
-    store_f<ST, 2>(a, o, fo[2]); store_h<ST, 2>(a, o, ho[2]);
-    store_f<ST, 3>(a, o, fo[3]); store_h<ST, 3>(a, o, ho[3]);
-    store_f<ST, 4>(a, o, fo[4]); store_h<ST, 4>(a, o, ho[4]);
-    store_f<ST, 5>(a, o, fo[5]); store_h<ST, 5>(a, o, ho[5]);
-    store_f<ST, 6>(a, o, fo[6]); store_h<ST, 6>(a, o, ho[6]);
-    store_f<ST, 7>(a, o, fo[7]); store_h<ST, 7>(a, o, ho[7]);
-    store_f<ST, 8>(a, o, fo[8]); store_h<ST, 8>(a, o, ho[8]);
+    store_fs<ST, 0>(a, o, fo[0]); store_hs<ST, 0>(a, o, ho[0]);
+    store_fs<ST, 1>(a, o, fo[1]); store_hs<ST, 1>(a, o, ho[1]);
+    store_fs<ST, 2>(a, o, fo[2]); store_hs<ST, 2>(a, o, ho[2]);
+    store_fs<ST, 3>(a, o, fo[3]); store_hs<ST, 3>(a, o, ho[3]);
+    store_fs<ST, 4>(a, o, fo[4]); store_hs<ST, 4>(a, o, ho[4]);
+    store_fs<ST, 5>(a, o, fo[5]); store_hs<ST, 5>(a, o, ho[5]);
+    store_fs<ST, 6>(a, o, fo[6]); store_hs<ST, 6>(a, o, ho[6]);
+    store_fs<ST, 7>(a, o, fo[7]); store_hs<ST, 7>(a, o, ho[7]);
+    store_fs<ST, 8>(a, o, fo[8]); store_hs<ST, 8>(a, o, ho[8]);
 
     if (!kIn && L.wall) {
       // Ladd half-way bounce-back (Sec. 4): a population heading into the
@@ -799,29 +805,32 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       // beyond a free-slip side wall the ghost-row slot of x -+ 1 is the
       // mirror direction's slot in this column (where the specular pull reads)
       const bool lw = kXw && gx == 0, rw = kXw && gx == L.nx - 1;
+      // diagonal weight w_5..8 (float32), or the storage scale in which
+      // 2 w_i rho c_i.u_w / w_i is 2 rho c_i.u_w 2^s
+      const float bwf = kScaled ? P.sf : qw(7), bwh = kScaled ? P.sh : qw(7);
       if (gy == 0) {
         const float uw = P.uwb;
         // i = 4 (0,-1) -> opp 2 at (x, -1); i = 7 (-1,-1) -> opp 5 at (x-1, -1);
         // i = 8 (1,-1) -> opp 6 at (x+1, -1)
-        store_f<ST, 2>(a, gx, fo[4]);
-        store_h<ST, 2>(a, gx, ho[4]);
-        const float f5 = fo[7] - 2.0f * qw(7) * rho * (-uw);
-        const float h5 = ho[7] - 2.0f * qw(7) * phi * 3.0f * (-uw);
+        store_fs<ST, 2>(a, gx, fo[4]);
+        store_hs<ST, 2>(a, gx, ho[4]);
+        const float f5 = fo[7] - 2.0f * bwf * rho * (-uw);
+        const float h5 = ho[7] - 2.0f * bwh * phi * 3.0f * (-uw);
         if (lw) {
-          store_f<ST, 6>(a, gx, f5);
-          store_h<ST, 6>(a, gx, h5);
+          store_fs<ST, 6>(a, gx, f5);
+          store_hs<ST, 6>(a, gx, h5);
         } else {
-          store_f<ST, 5>(a, xl, f5);
-          store_h<ST, 5>(a, xl, h5);
+          store_fs<ST, 5>(a, xl, f5);
+          store_hs<ST, 5>(a, xl, h5);
         }
-        const float f6 = fo[8] - 2.0f * qw(8) * rho * uw;
-        const float h6 = ho[8] - 2.0f * qw(8) * phi * 3.0f * uw;
+        const float f6 = fo[8] - 2.0f * bwf * rho * uw;
+        const float h6 = ho[8] - 2.0f * bwh * phi * 3.0f * uw;
         if (rw) {
-          store_f<ST, 5>(a, gx, f6);
-          store_h<ST, 5>(a, gx, h6);
+          store_fs<ST, 5>(a, gx, f6);
+          store_hs<ST, 5>(a, gx, h6);
         } else {
-          store_f<ST, 6>(a, xr, f6);
-          store_h<ST, 6>(a, xr, h6);
+          store_fs<ST, 6>(a, xr, f6);
+          store_hs<ST, 6>(a, xr, h6);
         }
       }
       if (gy == L.ny - 1) {
@@ -829,25 +838,25 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
         const int g = (L.ny + 1) * L.nx;
         // i = 2 (0,1) -> opp 4 at (x, ny); i = 5 (1,1) -> opp 7 at (x+1, ny);
         // i = 6 (-1,1) -> opp 8 at (x-1, ny)
-        store_f<ST, 4>(a, g + gx, fo[2]);
-        store_h<ST, 4>(a, g + gx, ho[2]);
-        const float f7 = fo[5] - 2.0f * qw(5) * rho * uw;
-        const float h7 = ho[5] - 2.0f * qw(5) * phi * 3.0f * uw;
+        store_fs<ST, 4>(a, g + gx, fo[2]);
+        store_hs<ST, 4>(a, g + gx, ho[2]);
+        const float f7 = fo[5] - 2.0f * bwf * rho * uw;
+        const float h7 = ho[5] - 2.0f * bwh * phi * 3.0f * uw;
         if (rw) {
-          store_f<ST, 8>(a, g + gx, f7);
-          store_h<ST, 8>(a, g + gx, h7);
+          store_fs<ST, 8>(a, g + gx, f7);
+          store_hs<ST, 8>(a, g + gx, h7);
         } else {
-          store_f<ST, 7>(a, g + xr, f7);
-          store_h<ST, 7>(a, g + xr, h7);
+          store_fs<ST, 7>(a, g + xr, f7);
+          store_hs<ST, 7>(a, g + xr, h7);
         }
-        const float f8 = fo[6] - 2.0f * qw(6) * rho * (-uw);
-        const float h8 = ho[6] - 2.0f * qw(6) * phi * 3.0f * (-uw);
+        const float f8 = fo[6] - 2.0f * bwf * rho * (-uw);
+        const float h8 = ho[6] - 2.0f * bwh * phi * 3.0f * (-uw);
         if (lw) {
-          store_f<ST, 7>(a, g + gx, f8);
-          store_h<ST, 7>(a, g + gx, h8);
+          store_fs<ST, 7>(a, g + gx, f8);
+          store_hs<ST, 7>(a, g + gx, h8);
         } else {
-          store_f<ST, 8>(a, g + xl, f8);
-          store_h<ST, 8>(a, g + xl, h8);
+          store_fs<ST, 8>(a, g + xl, f8);
+          store_hs<ST, 8>(a, g + xl, h8);
         }
       }
     }
