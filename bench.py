@@ -479,6 +479,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ckpt-every", type=int, default=200,
+                    help="adjoint workloads: checkpoint interval of the gradient run")
     ap.add_argument("--no-l2x", action="store_true",
                     help="skip the extra 2048 x 4096 (larger than L2) measurement")
     args = ap.parse_args()
@@ -505,8 +507,9 @@ def run_adjoint(args):
     """Adjoint pattern on the drop-in-shear workload (512 x 256, walls at
     -/+0.01, drop R = 40, Re = 1, Ca = 0.2, W = 4, M = 0.05, form --form):
     `--steps` forward steps, then the full gradient run (forward with a
-    checkpoint every 200 steps, recomputation of each segment, reverse
-    sweep).  Reported: GLUPS of the forward, time of the gradient run over the
+    checkpoint every `--ckpt-every` steps, 200 by default, recomputation of
+    each segment, reverse sweep; --ckpt-every >= --steps keeps the whole tape
+    of one segment taped in the forward run, with no recomputation).  Reported: GLUPS of the forward, time of the gradient run over the
     time of the forward, and the relative change of the gradients between
     checkpoint intervals 200 and 50 (a consistency figure)."""
     import torch
@@ -520,7 +523,7 @@ def run_adjoint(args):
     # radius and wall speed scaled to keep Re and Ca)
     s = int(args.workload.rsplit("_x", 1)[1]) if "_x" in args.workload else 1
     c = wl.shear_drop(args.form, nx=512 * s, ny=256 * s, R=40.0 * s, U=0.01)
-    T, every = args.steps, min(200, args.steps)
+    T, every = args.steps, min(args.ckpt_every, args.steps)
     stream = torch.cuda.Stream(dev)
     d = pflbm.Domain(c.nx, c.ny, wall_y=True, stream=stream, device=dev).set_params(**c.params)
     phi0 = torch.from_numpy(c.phi0.astype(np.float32)).to(dev)
