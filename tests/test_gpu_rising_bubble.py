@@ -6,14 +6,18 @@ rise velocity and circularity sampled through pflbm_bubble_diagnostics.
 Checked: the run stays finite; the mirror symmetry of the problem about the
 vertical midline holds (x-centroid on the midline); the centre of mass rises
 monotonically; and the paper's benchmark quantities fall in sanity bands
-around its printed values (Table rising: y_c max 1.0536-1.0681 m, v_c max
-0.2223-0.2284 m/s, circularity min 0.8889-0.9004 at 240 x 480).  Measured
+around its printed values (Table rising, tests/golden/rising_bubble_table.json:
+y_c max 1.0536-1.0681 m, v_c max 0.2223-0.2284 m/s, circularity min
+0.8889-0.9004 at 240 x 480).  Measured
 here: STF/CPF/PF forms v_max 0.195-0.199 m/s, y_c(3 s) 0.971-0.985 m,
 C_min 0.955-0.962; CSF-1 0.217 / 1.077 / 0.962; CSF-2 0.236 / 1.067 / 0.894.
 These are bands, not parity: the paper does not give its mobility or
 interface width (the workload's choices are those every form is stable
 with), and the parity of the quantities themselves is tested against the
 oracle in test_gpu_bubble.py."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -22,6 +26,14 @@ from paper_2012_14729_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 FORMS = ("STF1", "STF2", "CPF1", "CPF2", "PF1", "PF2", "CSF1", "CSF2")
+TABLE = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                    "rising_bubble_table.json")))
+
+
+def _band(key, lo, hi):
+    """[lo x the smallest printed value over the forms, hi x the reference]."""
+    vals = [v[key] for v in TABLE["forms"].values()]
+    return lo * min(vals), hi * TABLE["reference"][key]
 
 
 @pytest.fixture(scope="module")
@@ -59,8 +71,12 @@ def test_rising_bubble_to_three_seconds(pf, form):
         C.append(g["circularity"])
     assert t[-1] == pytest.approx(3.0, abs=m["s_per_step"])
     assert np.all(np.diff(yc) >= -1e-6), form
-    assert 0.18 <= max(vc) <= 0.26, (form, max(vc))
-    assert 0.85 <= min(C) <= 0.98, (form, min(C))
-    assert 0.95 <= yc[-1] <= 1.12, (form, yc[-1])
+    # bands: v_max [0.178, 0.266], C_min [0.844, 0.982], y_max [0.948, 1.125]
+    lo, hi = _band("v_max", 0.8, 1.1)
+    assert lo <= max(vc) <= hi, (form, max(vc))
+    lo, hi = _band("C_min", 0.95, 1.09)
+    assert lo <= min(C) <= hi, (form, min(C))
+    lo, hi = _band("y_max", 0.9, 1.04)
+    assert lo <= max(yc) <= hi, (form, max(yc))
     # the bubble starts round and at rest
     assert C[0] == pytest.approx(1.0, abs=5e-3) and abs(vc[0]) < 0.02
