@@ -128,3 +128,24 @@ def test_side_walls_state_round_trip_and_refusals(pf):
     with pytest.raises(pf.PflbmError):
         pf.Batch([a])
     assert pf.pflbm_adjoint_scratch_bytes(a.h, 10, 5) == 0
+
+
+@pytest.mark.parametrize("form", ["STF1", "CSF2"])
+def test_x_independent_state_ignores_the_side_walls(pf, form):
+    """A flat interface (phi independent of x) under gravity along y never
+    feels mirror planes in x: the side-wall run equals the periodic run to
+    float32 rounding (separately compiled kernels)."""
+    nx, ny = 70, 45
+    y = np.arange(ny, dtype=np.float64)[:, None] + np.zeros((1, nx))
+    phi0 = np.tanh(2.0 * (20.3 - y) / 4.0).astype(np.float32)
+    p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.25, nu1=0.1, nu2=0.2, gy=-1e-5,
+             form=form)
+    out = []
+    for wall_x in (True, False):
+        d = pf.Domain(nx, ny, wall_y=True, wall_x=wall_x).set_params(**p).init_phi(phi0)
+        d.step(300)
+        out.append(d.fields())
+    for k in ("phi", "ux", "uy", "P"):
+        scale = float(np.abs(out[1][k]).max()) + 1e-12
+        assert float(np.abs(out[0][k] - out[1][k]).max()) <= 1e-5 * scale, k
+    assert float(np.abs(out[0]["ux"]).max()) <= 1e-6
