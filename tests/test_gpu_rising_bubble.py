@@ -46,15 +46,25 @@ def pf():
     return pflbm
 
 
+# (nx, settings): the workload's defaults on 120 x 240; on the paper's finer
+# 240 x 480 grid the setting of the same width W = 8 that every form but
+# CPF-1 runs to 3 s with (CPF-1 diverges there after about 7200 steps)
+GRIDS = {120: {}, 240: dict(Ug=0.02, W=8.0, M=0.1, tau_h=0.8)}
+
+
+@pytest.mark.parametrize("nx", [120, 240])
 @pytest.mark.parametrize("form", FORMS)
-def test_rising_bubble_to_three_seconds(pf, form):
-    c = wl.rising_bubble(form, nx=120)
+def test_rising_bubble_to_three_seconds(pf, form, nx):
+    if nx == 240 and form == "CPF1":
+        pytest.skip("CPF-1 diverges on 240 x 480 with these settings")
+    c = wl.rising_bubble(form, nx=nx, **GRIDS[nx])
     d = pf.Domain(c.nx, c.ny, wall_y=True, wall_x=True).set_params(**c.params)
     d.init_phi(c.phi0.astype(np.float32))
     m = c.meta
     nsteps = int(round(3.0 / m["s_per_step"]))
     every = nsteps // 150
     mid = 0.5 * c.nx - 0.5
+    tol_mid = 2e-3 * c.nx / 120
     t, yc, vc, C = [], [], [], []
     n = 0
     while n < nsteps:
@@ -64,7 +74,7 @@ def test_rising_bubble_to_three_seconds(pf, form):
         g = d.bubble_diagnostics()
         assert g["status"] == "PFLBM_OK", (form, n)
         # mirror symmetry about the midline, up to float32 rounding order
-        assert abs(g["xc2"] - mid) < 2e-3, (form, n, g["xc2"])
+        assert abs(g["xc2"] - mid) < tol_mid, (form, n, g["xc2"])
         t.append(n * m["s_per_step"])
         yc.append((g["yc2"] + 0.5) * m["m_per_node"])
         vc.append(g["vc2"] * m["mps_per_lattice"])
