@@ -48,7 +48,8 @@ def pf():
 
 # (nx, settings): the workload's defaults on 120 x 240; on the paper's finer
 # 240 x 480 grid the setting of the same width W = 8 that every form but
-# CPF-1 runs to 3 s with (CPF-1 diverges there after about 7200 steps)
+# CPF-1 runs to 3 s with (CPF-1 diverges there: the FP64 oracle between
+# steps 7400 and 7600, the GPU by step 7224)
 GRIDS = {120: {}, 240: dict(Ug=0.02, W=8.0, M=0.1, tau_h=0.8)}
 
 
