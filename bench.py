@@ -406,6 +406,10 @@ def run_ours(args, case):
     # per step), timed over consecutive steps without flushing
     l2x = (measure_l2_exceeding(args, dev, wall_x=wall_x)
            if ws == 1 and not args.no_l2x and case.nx * case.ny < (1 << 23) else None)
+    # the patterns against this plain FP32 line (default workload, one GPU)
+    patterns = (measure_patterns(args, case, dev, value)
+                if ws == 1 and not args.no_patterns and args.storage == "fp32" and not wall_x
+                else None)
 
     line = {
         "metric": "GLUPS (coupled f+h step)", "value": value, "unit": "GLUPS",
@@ -426,6 +430,8 @@ def run_ours(args, case):
     }
     if l2x is not None:
         line["l2_exceeding"] = l2x
+    if patterns is not None:
+        line["patterns"] = patterns
     if wall_x:
         line["bubble_diagnostics"] = time_bubble_diagnostics(dom, case)
     print(json.dumps(line), flush=True)
@@ -479,6 +485,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the 16-bit, batch and adjoint measurements of the default line")
     ap.add_argument("--ckpt-every", type=int, default=200,
                     help="adjoint workloads: checkpoint interval of the gradient run")
     ap.add_argument("--no-l2x", action="store_true",
@@ -504,6 +512,10 @@ def main():
 
 
 def run_adjoint(args):
+    print(json.dumps(measure_adjoint(args)), flush=True)
+
+
+def measure_adjoint(args, consistency=True):
     """Adjoint pattern on the drop-in-shear workload (512 x 256, walls at
     -/+0.01, drop R = 40, Re = 1, Ca = 0.2, W = 4, M = 0.05, form --form):
     `--steps` forward steps, then the full gradient run (forward with a
@@ -550,11 +562,15 @@ def run_adjoint(args):
     t0 = time.perf_counter()
     ds, dm = pflbm.pflbm_adjoint_run(d.h, phi0, T, every, g, dphi0, scratch)
     t_adj = (time.perf_counter() - t0) * 1e3
+    del scratch
     every2 = max(1, every // 4)
-    scratch2 = torch.empty(pflbm.pflbm_adjoint_scratch_bytes(d.h, T, every2), dtype=torch.uint8,
-                           device=dev)
-    dphi0b = torch.empty_like(phi0)
-    ds2, dm2 = pflbm.pflbm_adjoint_run(d.h, phi0, T, every2, g, dphi0b, scratch2)
+    rel = None
+    if consistency:
+        scratch2 = torch.empty(pflbm.pflbm_adjoint_scratch_bytes(d.h, T, every2),
+                               dtype=torch.uint8, device=dev)
+        dphi0b = torch.empty_like(phi0)
+        ds2, dm2 = pflbm.pflbm_adjoint_run(d.h, phi0, T, every2, g, dphi0b, scratch2)
+        rel = max(abs(ds2 / ds - 1), abs(dm2 / dm - 1))
     nodes = c.nx * c.ny
     line = {
         "metric": "GLUPS (coupled f+h step)", "value": nodes * T / (t_fwd * 1e-3) / 1e9,
@@ -565,18 +581,23 @@ def run_adjoint(args):
                    "ckpt_every": every},
         "adjoint": {"gradient_run_ms": t_adj, "forward_ms": t_fwd,
                     "cost_over_forward": t_adj / t_fwd,
-                    "dJ_dsigma": ds, "dJ_dM": dm,
-                    "rel_change_ckpt_every_%d" % every2: max(abs(ds2 / ds - 1), abs(dm2 / dm - 1))},
+                    "dJ_dsigma": ds, "dJ_dM": dm},
     }
-    print(json.dumps(line), flush=True)
+    if rel is not None:
+        line["adjoint"]["rel_change_ckpt_every_%d" % every2] = rel
+    return line
 
 
 def run_batch(args):
+    print(json.dumps(measure_batch(args)), flush=True)
+
+
+def measure_batch(args, clocks=True):
     """Batched pattern, workload batchN (batch256 is the configuration): N
     drop instances (L from {64, 128, 256, 512}, R in [0.15, 0.35] L, sigma
     log-uniform in [1e-4, 1e-2], force family cycling STF, CPF, PF, CSF),
     FP32, one persistent launch per step replayed from a CUDA graph,
-    autotuned; for N = 256 about 22 M nodes (3.6 GB of state per step,
+    autotuned; for N = 256 about 24 M nodes (3.6 GiB of state per step,
     larger than L2).  Also timed: the same instances stepped one launch
     each."""
     import torch
@@ -609,11 +630,13 @@ def run_batch(args):
         stream.synchronize()
         return e0.elapsed_time(e1)
 
-    clk = ClockSampler(torch.cuda.current_device())
-    clk.__enter__()
+    if clocks:
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.__enter__()
     t_ms = timed(b.step, args.steps)
-    time.sleep(0.15)
-    clk.__exit__(None, None, None)
+    if clocks:
+        time.sleep(0.15)
+        clk.__exit__(None, None, None)
     diag = doms[0].diagnostics()
 
     # the same instances, one launch per instance and step (autotuned each)
@@ -648,9 +671,68 @@ def run_batch(args):
         "per_instance_launches": {"value": nodes * k_solo / (t_solo * 1e-3) / 1e9,
                                   "unit": "GLUPS", "launches_per_step": len(doms)},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if clocks:
+        line["clocks"] = clk.summary()
+    return line
+
+
+def measure_storage(args, case, dev, storage, steps):
+    """GLUPS of the timed workload with another population storage, timed
+    like the main line (L2 flushed before every step, CUDA events per step)."""
+    import torch
+    from paper_2012_14729_gb300 import pflbm
+    dom = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y,
+                       wall_x=case.meta.get("wall_x", False), storage=storage, device=dev)
+    dom.set_params(**case.params)
+    dom.init_phi(case.phi0.astype(np.float32))
+    stage = dom.autotune(10)
+    flush = ColdL2(dev)
+    stream = dom.stream
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            flush()
+            dom.step(1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            flush()
+            e0.record(stream)
+            dom.step(1)
+            e1.record(stream)
+    stream.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps
+    n = case.nx * case.ny
+    peak, _ = measured_peaks()
+    return {"value": n / (ms * 1e-3) / 1e9, "unit": "GLUPS", "ms_per_step": ms,
+            "stage": stage, "roofline_frac": BYTES_PER_LUP[storage] * n / (ms * 1e-3) / 1e9 / peak,
+            "state_status": dom.diagnostics()["status"]}
+
+
+def measure_patterns(args, case, dev, plain_value):
+    """The three patterns against the plain FP32 step, measured in this run:
+    16-bit storage on the timed workload, the 256-instance batch against the
+    same instances launched one by one, and the adjoint of the 512 x 256
+    drop in shear (4000 steps, checkpoint every 200) against its forward."""
+    import argparse as _ap
+    out = {"plain_fp32": {"value": plain_value, "unit": "GLUPS"}}
+    for st in ("fp16", "bf16"):
+        r = measure_storage(args, case, dev, st, args.steps)
+        r["vs_plain"] = r["value"] / plain_value
+        out[st] = r
+    b = measure_batch(_ap.Namespace(workload="batch256", steps=20, warmup=5), clocks=False)
+    out["batch256"] = {"value": b["value"], "unit": "GLUPS", "config": b["config"],
+                       "per_instance_launches": b["per_instance_launches"]["value"],
+                       "vs_per_instance_launches":
+                           b["value"] / b["per_instance_launches"]["value"]}
+    a = measure_adjoint(_ap.Namespace(workload="adjoint_shear", steps=4000, warmup=10,
+                                      form="STF1", ckpt_every=200), consistency=False)
+    out["adjoint_shear"] = {"cost_over_forward": a["adjoint"]["cost_over_forward"],
+                            "forward_glups": a["value"], "steps": 4000, "ckpt_every": 200,
+                            "form": "STF1"}
+    return out
 
 
 if __name__ == "__main__":

@@ -110,7 +110,7 @@ def test_side_wall_workload_2048x4096_sampled(pf, orc):
 
 
 def test_batch_of_256_instances_sampled(pf, orc):
-    """The 256-instance batch (22 M nodes, one persistent launch per step,
+    """The 256-instance batch (24 M nodes, one persistent launch per step,
     the autotuned configuration): one batch step of sampled whole instances
     against one oracle step from the same state."""
     cases = wl.batch_instances(256)
