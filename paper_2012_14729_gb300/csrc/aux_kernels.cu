@@ -142,6 +142,9 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Blocks take rows (grid-stride), threads take columns of a row; the y
+// moments are formed once per row from the thread's row sums of w and w x,
+// which keeps the FP64 work per node to the x moments (FP64 is slow here).
 __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
                                                                const float* __restrict__ fields,
                                                                const DiagGeom g,
@@ -150,40 +153,49 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
   double acc[13];
 #pragma unroll
   for (int j = 0; j < 13; ++j) acc[j] = 0.0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int y = k / L.nx, x = k - y * L.nx;
-    const double phi = fields[k];
-    const double ux = fields[2 * n + k], uy = fields[3 * n + k];
-    const double ph = fields[6 * n + k];
-    const bool finite = isfinite(phi) && isfinite(ux) && isfinite(uy) && isfinite(ph) &&
-                        isfinite((double)fields[4 * n + k]);
-    if (!finite) {
-      acc[12] += 1.0;
-      continue;
-    }
-    const double w = 0.5 * (1.0 + phi);
-    acc[0] += phi;
-    acc[1] = fmax(acc[1], ux * ux + uy * uy);
-    acc[2] += w;
-    acc[3] += w * x;
-    acc[4] += w * y;
-    acc[5] += w * x * x;
-    acc[6] += w * y * y;
-    acc[7] += w * x * y;
-    if (g.has_geom) {
-      double dx = fabs(x - g.xc), dy = fabs(y - g.yc);
-      if (!L.wall_x) dx = fmin(dx, L.nx - dx);  // periodic distance across x
-      dy = fmin(dy, L.ny - dy);
-      const double r = sqrt(dx * dx + dy * dy);
-      if (r <= g.r_in) {
-        acc[8] += ph;
-        acc[9] += 1.0;
+  for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
+    const double yd = y;
+    double rw = 0.0, rwx = 0.0;  // this thread's sums of w and w x over the row
+    double dy = fabs(yd - g.yc);
+    dy = fmin(dy, L.ny - dy);
+    const int row = y * L.nx;
+    for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+      const int k = row + x;
+      const float phif = fields[k], uxf = fields[2 * n + k], uyf = fields[3 * n + k];
+      const float phf = fields[6 * n + k];
+      if (!(isfinite(phif) && isfinite(uxf) && isfinite(uyf) && isfinite(phf) &&
+            isfinite(fields[4 * n + k]))) {
+        acc[12] += 1.0;
+        continue;
       }
-      if (r >= g.r_out) {
-        acc[10] += ph;
-        acc[11] += 1.0;
+      const double phi = phif, ux = uxf, uy = uyf;
+      const double w = 0.5 * (1.0 + phi);
+      const double xd = x;
+      acc[0] += phi;
+      acc[1] = fmax(acc[1], ux * ux + uy * uy);
+      rw += w;
+      rwx += w * xd;
+      acc[5] += w * xd * xd;
+      if (g.has_geom) {
+        double dx = fabs(xd - g.xc);
+        if (!L.wall_x) dx = fmin(dx, L.nx - dx);  // periodic distance across x
+        const double r = sqrt(dx * dx + dy * dy);
+        const double ph = phf;
+        if (r <= g.r_in) {
+          acc[8] += ph;
+          acc[9] += 1.0;
+        }
+        if (r >= g.r_out) {
+          acc[10] += ph;
+          acc[11] += 1.0;
+        }
       }
     }
+    acc[2] += rw;
+    acc[3] += rwx;
+    acc[4] += rw * yd;
+    acc[6] += rw * yd * yd;
+    acc[7] += rwx * yd;
   }
   __shared__ double red[kDiagThreads / 32][13];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -268,33 +280,40 @@ __global__ void __launch_bounds__(kDiagThreads) k_bubble_partial(const Lattice L
   double acc[kBubbleSlots];
 #pragma unroll
   for (int j = 0; j < kBubbleSlots; ++j) acc[j] = 0.0;
+  int inside = 0;  // nodes with phi < 0
   const float* __restrict__ phi = fields;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int y = k / L.nx, x = k - y * L.nx;
-    const double p = phi[k];
-    const double ux = fields[2 * n + k], uy = fields[3 * n + k];
-    if (!(isfinite(p) && isfinite(ux) && isfinite(uy))) {
-      acc[7] += 1.0;
-      continue;
+  // blocks take rows, threads take columns (y moment once per row)
+  for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
+    double rw = 0.0;
+    const bool row_cells = y + 1 < L.ny || !L.wall;
+    const int r0 = y * L.nx, r1 = (y + 1 < L.ny ? y + 1 : 0) * L.nx;
+    for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+      const int k = r0 + x;
+      const float pf = phi[k], uxf = fields[2 * n + k], uyf = fields[3 * n + k];
+      if (!(isfinite(pf) && isfinite(uxf) && isfinite(uyf))) {
+        acc[7] += 1.0;
+        continue;
+      }
+      const double w = 1.0 - (double)pf;
+      rw += w;
+      acc[1] += w * x;
+      acc[3] += w * (double)uxf;
+      acc[4] += w * (double)uyf;
+      inside += pf < 0.0f ? 1 : 0;
+      if (row_cells && (x + 1 < L.nx || !L.wall_x)) {
+        const int x1 = x + 1 < L.nx ? x + 1 : 0;
+        const float c1 = phi[r0 + x1], c2 = phi[r1 + x1], c3 = phi[r1 + x];
+        // a non-finite corner is counted at its own node; its cells add nothing
+        const float lo = fminf(fminf(pf, c1), fminf(c2, c3));
+        const float hi = fmaxf(fmaxf(pf, c1), fmaxf(c2, c3));
+        if (lo < 0.0f && hi >= 0.0f && isfinite(c1) && isfinite(c2) && isfinite(c3))
+          acc[6] += cell_contour(pf, c1, c2, c3);
+      }
     }
-    const double w = 1.0 - p;
-    acc[0] += w;
-    acc[1] += w * x;
-    acc[2] += w * y;
-    acc[3] += w * ux;
-    acc[4] += w * uy;
-    acc[5] += p < 0.0 ? 1.0 : 0.0;
-    const bool has_cell = (x + 1 < L.nx || !L.wall_x) && (y + 1 < L.ny || !L.wall);
-    if (has_cell) {
-      const int x1 = x + 1 < L.nx ? x + 1 : 0;
-      const int r1 = (y + 1 < L.ny ? y + 1 : 0) * L.nx;
-      const double c1 = phi[y * L.nx + x1], c2 = phi[r1 + x1], c3 = phi[r1 + x];
-      const double lo = fmin(fmin(p, c1), fmin(c2, c3)), hi = fmax(fmax(p, c1), fmax(c2, c3));
-      // a non-finite corner is counted at its own node; its cells add nothing
-      if (lo < 0.0 && hi >= 0.0 && isfinite(c1) && isfinite(c2) && isfinite(c3))
-        acc[6] += cell_contour(p, c1, c2, c3);
-    }
+    acc[0] += rw;
+    acc[2] += rw * y;
   }
+  acc[5] = inside;
   __shared__ double red[kDiagThreads / 32][kBubbleSlots];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -311,15 +330,13 @@ __global__ void __launch_bounds__(kDiagThreads) k_bubble_partial(const Lattice L
   }
 }
 
-int diag_blocks(int n_nodes, int max_blocks) {
-  int b = (n_nodes + kDiagThreads - 1) / kDiagThreads;
-  if (b > max_blocks) b = max_blocks;
-  return b < 1 ? 1 : b;
-}
+
+// one block per row, up to max_blocks (then rows grid-stride)
+int row_blocks(int ny, int max_blocks) { return ny < max_blocks ? (ny > 0 ? ny : 1) : max_blocks; }
 
 cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, double* partials,
                         int max_blocks, double* red, cudaStream_t s) {
-  const int nb = diag_blocks(L.nx * L.ny, max_blocks);
+  const int nb = row_blocks(L.ny, max_blocks);
   k_diag_partial<<<nb, kDiagThreads, 0, s>>>(L, fields, g, partials);
   k_diag_final<<<1, 32 * kNRed, 0, s>>>(partials, nb, 13, 1, red);
   return cudaGetLastError();
@@ -327,7 +344,7 @@ cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, doubl
 
 cudaError_t launch_bubble_diag(const Lattice& L, const float* fields, double* partials,
                                int max_blocks, double* red, cudaStream_t s) {
-  const int nb = diag_blocks(L.nx * L.ny, max_blocks);
+  const int nb = row_blocks(L.ny, max_blocks);
   k_bubble_partial<<<nb, kDiagThreads, 0, s>>>(L, fields, partials);
   k_diag_final<<<1, 32 * kNRed, 0, s>>>(partials, nb, kBubbleSlots, -1, red);
   return cudaGetLastError();

@@ -166,7 +166,6 @@ struct DiagGeom {
 // FP64 reductions of the staged fields into red[kNRed] (partials in scratch).
 cudaError_t launch_diag(const Lattice& L, const float* fields, DiagGeom g, double* partials,
                         int max_blocks, double* red, cudaStream_t s);
-int diag_blocks(int n_nodes, int max_blocks);
 // Rising-bubble sums of the staged fields (fluid-2 moments, phi < 0 count,
 // marching-squares contour length) into red[0..7].
 cudaError_t launch_bubble_diag(const Lattice& L, const float* fields, double* partials,
