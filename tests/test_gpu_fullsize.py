@@ -156,9 +156,10 @@ def test_batch_of_256_instances_sampled(pf, orc):
 def test_adjoint_of_the_shear_drop_at_full_size(pf, orc, form):
     """The adjoint configuration itself (512 x 256 drop in shear, 4000 steps,
     checkpoint every 200) with its mismatch objective J = sum (phi_T -
-    target)^2: dJ/dsigma and dJ/dM of the GPU adjoint against central
-    differences of the FP64 oracle (the FP64 reference gradient) at 1e-4
-    relative steps; bound 1e-3 relative (measured 1e-5 to 4e-4).
+    target)^2: dJ/dsigma, dJ/dM and dJ/dphi0 along a bump on the drop's
+    interface, of the GPU adjoint against central differences of the FP64
+    oracle (the FP64 reference gradient) at 1e-4 relative steps; bound 1e-3
+    relative (measured 1e-5 to 4e-4 for sigma and M).
 
     Two things this case does not allow.  Differences of the float32 GPU
     forward: a 1 % step moves J by 4e-6 of J, the size of float32 rounding
@@ -188,9 +189,9 @@ def test_adjoint_of_the_shear_drop_at_full_size(pf, orc, form):
     d.synchronize()
     adj = pf.pflbm_adjoint_run(d.h, phi0, T, K, g, dphi0, scratch)
 
-    def J(**kw):
-        s = orc.Sim(c.nx, c.ny, True, orc.Params(**{**c.params, **kw}),
-                    phi0_32.astype(np.float64)).step(T)
+    def J(phi0_64=None, **kw):
+        p0 = phi0_32.astype(np.float64) if phi0_64 is None else phi0_64
+        s = orc.Sim(c.nx, c.ny, True, orc.Params(**{**c.params, **kw}), p0).step(T)
         return float(np.sum((s.h.sum(0) - target) ** 2))
     e = 1e-4
     for k, pname in enumerate(("sigma", "M")):
@@ -198,3 +199,12 @@ def test_adjoint_of_the_shear_drop_at_full_size(pf, orc, form):
         f = (J(**{pname: v0 * (1 + e)}) - J(**{pname: v0 * (1 - e)})) / (2 * e * v0)
         print(f"{form} dJ/d{pname}: adjoint {adj[k]:.6e}  FP64 differences {f:.6e}")
         assert abs(adj[k] - f) <= 1e-3 * abs(f), (form, pname, adj[k], f)
+    # direction in phi0: a Gaussian bump of width 6 on the interface, right of the drop
+    y, x = np.mgrid[0:c.ny, 0:c.nx].astype(np.float64)
+    v = np.exp(-((x - (c.nx / 2 + c.meta["R"])) ** 2 + (y - c.ny / 2) ** 2) / (2 * 6.0 ** 2))
+    a_dir = float(np.sum(dphi0.cpu().numpy().astype(np.float64) * v))
+    eps = 1e-4
+    p0 = phi0_32.astype(np.float64)
+    f_dir = (J(p0 + eps * v) - J(p0 - eps * v)) / (2 * eps)
+    print(f"{form} dJ/dphi0 . v: adjoint {a_dir:.6e}  FP64 differences {f_dir:.6e}")
+    assert abs(a_dir - f_dir) <= 1e-3 * abs(f_dir), (form, a_dir, f_dir)
