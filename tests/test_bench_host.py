@@ -71,3 +71,24 @@ def test_job_throughput_and_algorithmic_bytes():
     assert bench.BYTES_PER_LUP["fp32"] == (18 * 2 + 2 * 2) * 4
     assert bench.BYTES_PER_LUP["fp16"] == 17 * 2 * 2 + (1 * 2 + 2 * 2) * 4
     assert bench.L2_FLUSH_BYTES > 129e6
+
+
+def test_pattern_failures_stay_in_their_entry(monkeypatch):
+    """A failing side measurement of the default line is reported in its
+    own entry; the others and the plain value are kept."""
+    def boom(*a, **k):
+        raise RuntimeError("out of memory")
+    monkeypatch.setattr(bench, "measure_storage",
+                        lambda args, case, dev, st, steps: {"value": 2.0, "unit": "GLUPS"})
+    monkeypatch.setattr(bench, "measure_batch", boom)
+    monkeypatch.setattr(bench, "measure_adjoint",
+                        lambda a, consistency=True: {"value": 13.0,
+                                                     "adjoint": {"cost_over_forward": 5.0}})
+
+    class Args:
+        steps = 3
+    out = bench.measure_patterns(Args(), None, None, 1.0)
+    assert out["plain_fp32"]["value"] == 1.0
+    assert out["fp16"]["vs_plain"] == 2.0 and out["bf16"]["value"] == 2.0
+    assert out["batch256"] == {"error": "RuntimeError: out of memory"}
+    assert out["adjoint_shear"]["cost_over_forward"] == 5.0
