@@ -313,21 +313,6 @@ __device__ __forceinline__ float pull_phi_s(const StepArgs& a, const Pull& q) {
 }
 
 template <class ST>
-__device__ __forceinline__ float pull_phi(const StepArgs& a, const Pull& q) {
-  // summed in direction order 0..8
-  float s = load_h<ST, 0>(a, q.i[0]);
-  s += load_h<ST, 1>(a, q.i[1]);
-  s += load_h<ST, 2>(a, q.i[2]);
-  s += load_h<ST, 3>(a, q.i[3]);
-  s += load_h<ST, 4>(a, q.i[4]);
-  s += load_h<ST, 5>(a, q.i[5]);
-  s += load_h<ST, 6>(a, q.i[6]);
-  s += load_h<ST, 7>(a, q.i[7]);
-  s += load_h<ST, 8>(a, q.i[8]);
-  return s;
-}
-
-template <class ST>
 __device__ __forceinline__ void pull_f(const StepArgs& a, const Pull& q, float* f) {
   f[0] = load_f<ST, 0>(a, q.i[0]);
   f[1] = load_f<ST, 1>(a, q.i[1]);
