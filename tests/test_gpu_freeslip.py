@@ -149,3 +149,18 @@ def test_x_independent_state_ignores_the_side_walls(pf, form):
         scale = float(np.abs(out[1][k]).max()) + 1e-12
         assert float(np.abs(out[0][k] - out[1][k]).max()) <= 1e-5 * scale, k
     assert float(np.abs(out[0]["ux"]).max()) <= 1e-6
+
+
+def test_side_walls_graph_replay_equals_plain_launches(pf):
+    nx, ny = 70, 45
+    phi0 = wl.drop(nx, ny, 10.0, 4.0, xc=4.3, yc=21.6, periodic_y=False).astype(np.float32)
+    p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.25, nu1=0.1, nu2=0.2, gy=-1e-5)
+    out = []
+    for graphs in (False, True):
+        d = pf.Domain(nx, ny, wall_y=True, wall_x=True).set_params(**p).init_phi(phi0)
+        d.graphs(graphs)
+        d.step(3)
+        d.step(40)
+        out.append(d.populations())
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
