@@ -182,3 +182,47 @@ def test_shear_wave_viscosity(orc):
         res.append(-math.log(a1 / a0) / 400 / (nu * k * k) - 1)
     assert abs(res[0]) < 4e-3 and abs(res[1]) < 1e-3
     assert abs(res[0] / res[1]) > 3.0
+
+
+def _smooth_periodic(L):
+    x = (np.arange(L) + 0.5) / L
+    X, Y = np.meshgrid(x, x)
+    t = 2 * np.pi
+    return 0.5 * np.cos(t * X + 0.3) * np.cos(t * Y - 0.7) + 0.3 * np.sin(2 * t * X + t * Y + 1.1) - 0.1
+
+
+def _spectral_curl(Fx, Fy):
+    # d Fy/dx - d Fx/dy of a periodic field, by FFT (independent of the ICS stencils)
+    L = Fx.shape[0]
+    k = np.fft.fftfreq(L) * 2 * np.pi
+    KX, KY = np.meshgrid(k, k)
+    return np.real(np.fft.ifft2(1j * KX * np.fft.fft2(Fy) - 1j * KY * np.fft.fft2(Fx)))
+
+
+def test_free_energy_forms_differ_by_a_gradient(orc):
+    """Sec. 2.2, Eq. identity: STF-1, STF-2, CPF-1, CPF-2, PF-1 and PF-2 are the
+    same force up to the gradient of a scalar absorbed into the pressure
+    (Eqs. SF1, SF2, SF3456 with P3456); the CSF forms are a different model.
+    A gradient field has zero curl: on a smooth periodic phi refined at fixed
+    shape, the curl of F_form - F_STF1 relative to k |F_form - F_STF1| must
+    vanish at second order for the six forms and stay O(1) for the CSF forms."""
+    r = {}
+    for L in (32, 64, 128):
+        phi = _smooth_periodic(L)
+        F = {}
+        for form in orc.FORMS:
+            p = orc.Params(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=1.0, nu1=0.1, nu2=0.1,
+                           form=form)
+            m = orc.Sim(L, L, False, p, phi).macro()
+            F[form] = (m["Fx"], m["Fy"])
+        k = 2 * np.pi / L
+        for form in orc.FORMS[1:]:
+            dx, dy = F[form][0] - F["STF1"][0], F[form][1] - F["STF1"][1]
+            mag = max(np.abs(dx).max(), np.abs(dy).max())
+            r[(form, L)] = float(np.abs(_spectral_curl(dx, dy)).max() / (k * mag))
+    for form in ("STF2", "CPF1", "CPF2", "PF1", "PF2"):
+        assert r[(form, 128)] < 5e-3, (form, r[(form, 128)])
+        # second order (or better) in the lattice spacing
+        assert r[(form, 64)] / r[(form, 128)] > 2.5, (form, r[(form, 64)], r[(form, 128)])
+    for form in ("CSF1", "CSF2"):
+        assert min(r[(form, L)] for L in (32, 64, 128)) > 0.3, form
