@@ -60,19 +60,37 @@ def wave_amplitude(phi: np.ndarray) -> float:
     return 0.5 * (interface_height(phi, 0) - interface_height(phi, nx // 2))
 
 
-def time_averaged_error(h_num, h_th) -> float:
-    """Time-averaged L2 error of an amplitude history (Table of Sec. 5.3),
-    read as sqrt(sum (h_num - h_th)^2 / sum h_th^2) over the samples."""
-    h_num = np.asarray(h_num, float)
-    h_th = np.asarray(h_th, float)
-    return float(np.sqrt(np.sum((h_num - h_th) ** 2) / np.sum(h_th ** 2)))
+def omega0(k: float, sigma: float, rho1: float, rho2: float) -> float:
+    """Inviscid capillary frequency, omega_0^2 = sigma k^3 / (rho1 + rho2)."""
+    return math.sqrt(sigma * k ** 3 / (rho1 + rho2))
 
 
-def run_capillary_wave(pflbm, case, steps: int, every: int):
+def time_averaged_error(t, h_num, h_th) -> float:
+    """E_2 of Eq. capilary_error: the root of the time average of
+    |h(t)/h0 - h_exact(t)/h0|^2 over the sampled window [t_0, t_end] (the
+    paper's window is [0, 25 / omega_0]), the integral taken by the
+    trapezoidal rule over the samples."""
+    t = np.asarray(t, float)
+    d2 = (np.asarray(h_num, float) - np.asarray(h_th, float)) ** 2
+    integral = float(np.sum(0.5 * (d2[1:] + d2[:-1]) * np.diff(t)))
+    return math.sqrt(integral / (t[-1] - t[0]))
+
+
+def error_window_steps(case, every: int) -> int:
+    """Steps covering the paper's error window [0, 25 / omega_0], rounded up
+    to a multiple of `every`."""
+    p = case.params
+    t_end = 25.0 / omega0(case.meta["k"], p["sigma"], p["rho1"], p["rho2"])
+    return int(math.ceil(t_end / every)) * every
+
+
+def run_capillary_wave(pflbm, case, every: int, steps=None):
     """Advance a capillary-wave case on the GPU (module `pflbm`, the CUDA
-    binding), sampling the amplitude every `every` steps; returns the
-    sample times, h_num / h0, the analytic h / h0 and their time-averaged
-    error."""
+    binding), sampling the amplitude every `every` steps over `steps` steps
+    (default: the error window [0, 25 / omega_0]); returns the sample times,
+    h_num / h0, the analytic h / h0 and E_2."""
+    if steps is None:
+        steps = error_window_steps(case, every)
     p = case.params
     d = pflbm.Domain(case.nx, case.ny, wall_y=True).set_params(**p)
     d.init_phi(case.phi0.astype(np.float32))
@@ -85,4 +103,4 @@ def run_capillary_wave(pflbm, case, steps: int, every: int):
         hs.append(wave_amplitude(d.read("phi")) / h0)
     ts = np.asarray(ts, float)
     th = prosperetti_amplitude(ts, p["nu1"], case.meta["k"], p["sigma"], p["rho1"], p["rho2"])
-    return ts, np.asarray(hs), th, time_averaged_error(hs, th)
+    return ts, np.asarray(hs), th, time_averaged_error(ts, hs, th)

@@ -61,5 +61,31 @@ def test_interface_height_and_error():
     phi = np.tanh(2 * (yi - y) / 4.0)
     assert v.interface_height(phi, 0) == pytest.approx(121.9, abs=0.05)
     assert v.wave_amplitude(phi) == pytest.approx(1.6, abs=0.05)
-    assert v.time_averaged_error([1, 2], [1, 2]) == 0.0
-    assert v.time_averaged_error([2, 4], [1, 2]) == pytest.approx(1.0)
+
+
+
+def test_time_averaged_error_is_the_rms_over_the_window():
+    """Eq. capilary_error: sqrt of the time average of the squared difference.
+    Closed forms: a constant offset d gives |d|; a sine difference over whole
+    periods gives amplitude / sqrt 2; a linear drift a t over [0, T] gives
+    a T / sqrt 3 (trapezoid error O(dt^2))."""
+    t = np.linspace(0.0, 10.0, 2001)
+    h = np.cos(t)
+    assert v.time_averaged_error(t, h, h) == 0.0
+    assert v.time_averaged_error(t, h + 0.3, h) == pytest.approx(0.3, rel=1e-12)
+    T = 4 * np.pi
+    t2 = np.linspace(0.0, T, 4001)
+    assert v.time_averaged_error(t2, 0.2 * np.sin(t2), 0 * t2) == pytest.approx(0.2 / math.sqrt(2),
+                                                                              rel=1e-6)
+    assert v.time_averaged_error(t2, 0.01 * t2, 0 * t2) == pytest.approx(0.01 * T / math.sqrt(3),
+                                                                       rel=1e-6)
+
+
+def test_error_window_is_25_over_omega0():
+    from paper_2012_14729_gb300 import workloads as wl
+    c = wl.capillary_wave("STF1", H=80)
+    w0 = v.omega0(c.meta["k"], c.params["sigma"], c.params["rho1"], c.params["rho2"])
+    # omega_0^2 = sigma k^3 / (rho1 + rho2)
+    assert w0 ** 2 == pytest.approx(c.params["sigma"] * (2 * math.pi / 80) ** 3 / 2.0)
+    n = v.error_window_steps(c, 90)
+    assert n % 90 == 0 and 25 / w0 <= n < 25 / w0 + 90
