@@ -343,14 +343,18 @@ static void macro_px(const double* p, int nx, int ny, int wall, const double* f,
       double P = sf + (ux * drx + uy * dry) / 6.0;
       m[M_P * n + k] = P;
       /* hydrodynamic pressure p_h from the generalised pressure of each
-       * form: P_stf-1 = p_h + kappa |grad phi|^2 (Eq. SF1), P_stf-2 = p_h
-       * (Eq. SF2), Eq. P3456 for CPF/PF, and P_csf = p_h */
+       * form: P_stf-2 = p_h (Eq. SF2), Eq. P3456 for CPF/PF, P_csf = p_h,
+       * and P_stf-1 = p_h - kappa |grad phi|^2.  Eq. SF1 prints the STF-1
+       * term with a plus sign, but F_stf-1 = F_stf-2 - kappa grad |grad phi|^2
+       * (Eqs. SF1, SF2) and the same momentum equation for both forms fix
+       * the minus sign, which is also the one Eq. P3456 implies through
+       * Eq. identity (P_pf-1 - P_stf-1 = kappa |grad phi|^2 / 2). */
       double g2 = m[M_GX * n + k] * m[M_GX * n + k] + m[M_GY * n + k] * m[M_GY * n + k];
       double f0 = beta * (1.0 - ph * ph) * (1.0 - ph * ph);
       double muk = m[M_MU * n + k], Lk = m[M_LAP * n + k];
       double ph_p = P;
       switch (form) {
-        case STF1: ph_p = P - kap * g2; break;
+        case STF1: ph_p = P + kap * g2; break;
         case CPF1: ph_p = P - f0 + ph * muk + 0.5 * kap * g2; break;
         case CPF2: ph_p = P - f0 + 0.5 * kap * g2; break;
         case PF1: ph_p = P + 0.5 * kap * g2; break;

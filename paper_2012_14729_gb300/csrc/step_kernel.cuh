@@ -687,7 +687,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       const float om = (1.0f - phi) * (1.0f + phi);
       const float f0e = 0.25f * P.beta4 * om * om;
       float ph = Pr;
-      if constexpr (FORM == kSTF1) ph = Pr - P.kappa * g2;
+      // p_h from the generalised pressure of the form (Eqs. SF2, P3456;
+      // STF-1: P = p_h - kappa |grad phi|^2, the sign that Eqs. SF1, SF2
+      // and P3456 imply together)
+      if constexpr (FORM == kSTF1) ph = Pr + P.kappa * g2;
       if constexpr (FORM == kCPF1) ph = Pr - f0e + phi * mu + 0.5f * P.kappa * g2;
       if constexpr (FORM == kCPF2) ph = Pr - f0e + 0.5f * P.kappa * g2;
       if constexpr (FORM == kPF1) ph = Pr + 0.5f * P.kappa * g2;
