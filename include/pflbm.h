@@ -359,12 +359,16 @@ void pflbm_batch_destroy(pflbm_batch* b);
  * memory budget.  There cudaMalloc can fail because the lattice holds nearly
  * all of HBM, and cudaFree waits for the whole device, so a per-call
  * allocation would stall the simulation's own streams.  Such callers cannot
- * lend this call a workspace either; it uses a device array compiled into
- * the library instead and makes no cudaMalloc, cudaFree or other allocating
- * call (its set-up included).
+ * lend this call a workspace either; it uses a 4 MiB device array compiled
+ * into the library instead, and a call makes no cudaMalloc, cudaFree or other
+ * allocating call.
  *
  *   nx, ny  lattice size; nx * ny <= PFLBM_NOALLOC_MAX_NODES, else EINVAL
  *           with the limit in pflbm_last_error()
+ *   bc_x    PFLBM_PERIODIC or PFLBM_FREESLIP, bc_y PFLBM_PERIODIC or
+ *           PFLBM_WALL: the sides of the lattice the fields come from; the
+ *           distance to the pressure-jump centre wraps only across periodic
+ *           sides (as in pflbm_diagnostics)
  *   fields  device memory of the current device, [PFLBM_NFIELDS][ny][nx]
  *           float32 as pflbm_read_fields writes it (slots phi, ux, uy, P,
  *           p_h are read); borrowed; a host pointer is rejected with EINVAL
@@ -372,16 +376,22 @@ void pflbm_batch_destroy(pflbm_batch* b);
  *   stream  cudaStream_t to run on (NULL: the legacy default stream); the
  *           call synchronises it before returning
  *
- * Set-up: the first call on each device resolves the scratch array's address
- * there (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  The array is shared by every caller in
- * the process on that device: calls that overlap (from two host threads, or
- * on two streams without ordering between them) race on it and may return
- * wrong values; serialise them.  Returns EUNSTABLE if a node is non-finite
- * (the struct is still filled), ECUDA on a CUDA error. */
-pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, const float* fields,
-                                             const pflbm_diag_geom* geom, pflbm_diag* out,
-                                             void* stream);
+ * Set-up: every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress).  The first call on a device loads the library's
+ * module that holds the array, and with CUDA's lazy module loading that is
+ * when the driver reserves the array's 4 MiB on the device; later calls only
+ * find it.  Make that first call before the simulation fills HBM and before
+ * any stream capture.  A device reset (cudaDeviceReset, or a reset of the
+ * primary context) unloads the module: the next call loads it again and is a
+ * first call in this sense.  The array is shared by every caller in the
+ * process on that device and keeps the last call's partial sums (a call
+ * clears the counter it needs itself): calls that overlap (from two host
+ * threads, or on two streams without ordering between them) race on it and
+ * may return wrong values; serialise them.  Returns EUNSTABLE if a node is
+ * non-finite (the struct is still filled), ECUDA on a CUDA error. */
+pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, pflbm_bc bc_x, pflbm_bc bc_y,
+                                             const float* fields, const pflbm_diag_geom* geom,
+                                             pflbm_diag* out, void* stream);
 
 /* ---- misc ---------------------------------------------------------------- */
 

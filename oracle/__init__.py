@@ -229,19 +229,22 @@ class Sim:
 # FP64 diagnostics (Sec. 5)
 # ---------------------------------------------------------------------------
 
-def laplace(fields: dict, xc: float, yc: float, R: float, W: float) -> dict:
+def laplace(fields: dict, xc: float, yc: float, R: float, W: float,
+            wrap_x: bool = True, wrap_y: bool = True) -> dict:
     """Laplace-law measurement (Sec. 5.1): R_num from the drop area, Delta p as
     the mean hydrodynamic pressure p_h inside r <= R/2 minus its mean outside
-    r >= R + 3W (periodic distance from the initial centre),
-    sigma_num = R_num Delta p."""
+    r >= R + 3W (distance from the initial centre, periodic across the sides
+    that are periodic), sigma_num = R_num Delta p."""
     phi, P = fields["phi"], fields["p_h"]
     ny, nx = phi.shape
     x = np.arange(nx)[None, :]
     y = np.arange(ny)[:, None]
     dx = np.abs(x - xc)
-    dx = np.minimum(dx, nx - dx)
+    if wrap_x:
+        dx = np.minimum(dx, nx - dx)
     dy = np.abs(y - yc)
-    dy = np.minimum(dy, ny - dy)
+    if wrap_y:
+        dy = np.minimum(dy, ny - dy)
     r = np.sqrt(dx * dx + dy * dy)
     inside = r <= R / 2
     outside = r >= R + 3 * W

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_partial(const Lattice L,
     const double yd = y;
     double rw = 0.0, rwx = 0.0;  // this thread's sums of w and w x over the row
     double dy = fabs(yd - g.yc);
-    dy = fmin(dy, L.ny - dy);
+    if (!L.wall) dy = fmin(dy, L.ny - dy);  // periodic distance across y
     const int row = y * L.nx;
     for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
       const int k = row + x;

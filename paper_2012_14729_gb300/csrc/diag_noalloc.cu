@@ -8,8 +8,6 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "pflbm.h"
 #include "internal.h"
 
@@ -22,7 +20,6 @@ static_assert(kRows * kThreads == PFLBM_NOALLOC_MAX_NODES, "whole blocks");
 constexpr int kRedOff = kRows * kNRed;               // final slots (doubles)
 constexpr int kTicketOff = kRedOff + kNRed;          // block-completion counter
 constexpr int kScratchDoubles = kTicketOff + 16;     // 128 bytes for the counter
-constexpr int kMaxDevices = 64;
 
 // partials [kRows][kNRed] | red [kNRed] | ticket (unsigned int) : 4 MiB + 256 B
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
@@ -41,9 +38,12 @@ __device__ __forceinline__ double warp_max(double v) {
 // Slots: 0 sum phi, 1 max |u|^2, 2 sum w, 3 sum w x, 4 sum w y, 5 sum w x^2,
 // 6 sum w y^2, 7 sum w x y, 8 sum p_h inside, 9 n inside, 10 sum p_h outside,
 // 11 n outside, 12 non-finite count; w = (1 + phi)/2 (Secs. 5.1, 5.2, 5.5).
+// wrap_x / wrap_y: the lattice is periodic in that direction, so the
+// distance to the pressure-jump centre is the periodic one there.
 __global__ void __launch_bounds__(kThreads)
-    k_diag_noalloc(const int nx, const int ny, const float* __restrict__ fields,
-                   const DiagGeom g, double* __restrict__ scratch) {
+    k_diag_noalloc(const int nx, const int ny, const int wrap_x, const int wrap_y,
+                   const float* __restrict__ fields, const DiagGeom g,
+                   double* __restrict__ scratch) {
   const int n = nx * ny;
   double acc[13];
 #pragma unroll
@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kThreads)
       acc[7] += w * x * y;
       if (g.has_geom) {
         double dx = fabs(x - g.xc), dy = fabs(y - g.yc);
-        dx = fmin(dx, nx - dx);
-        dy = fmin(dy, ny - dy);
+        if (wrap_x) dx = fmin(dx, nx - dx);
+        if (wrap_y) dy = fmin(dy, ny - dy);
         const double r = sqrt(dx * dx + dy * dy);
         if (r <= g.r_in) {
           acc[8] += ph;
@@ -121,20 +121,16 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next call
 }
 
-std::mutex g_setup_mu;
-double* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, resolved once
-// per device (the first call on each device loads this file's module there).
-cudaError_t scratch_address(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+// Device address of the scratch array on the current device.  It is looked
+// up on every call: the first lookup on a device loads this file's module
+// there (which reserves the array), later ones find the loaded module.  A
+// cached address would go stale when the application resets the device,
+// since the module is then loaded again, possibly elsewhere.
+cudaError_t scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -179,13 +175,20 @@ pflbm_status cuda_fail(const char* what, cudaError_t e) {
 
 using namespace pflbm;
 
-extern "C" pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, const float* fields,
+extern "C" pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, pflbm_bc bc_x,
+                                                        pflbm_bc bc_y, const float* fields,
                                                         const pflbm_diag_geom* geom,
                                                         pflbm_diag* out, void* stream) {
   char msg[384];
   if (nx <= 0 || ny <= 0 || !fields || !out) {
     set_last_error("pflbm_field_diagnostics_noalloc: nx, ny must be positive and fields, out "
                    "non-null");
+    return PFLBM_EINVAL;
+  }
+  if ((bc_x != PFLBM_PERIODIC && bc_x != PFLBM_FREESLIP) ||
+      (bc_y != PFLBM_PERIODIC && bc_y != PFLBM_WALL)) {
+    set_last_error("pflbm_field_diagnostics_noalloc: bc_x must be PFLBM_PERIODIC or "
+                   "PFLBM_FREESLIP, bc_y PFLBM_PERIODIC or PFLBM_WALL");
     return PFLBM_EINVAL;
   }
   const long long n = (long long)nx * ny;
@@ -200,10 +203,6 @@ extern "C" pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, const fl
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail("current device", e);
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_last_error("pflbm_field_diagnostics_noalloc: device ordinal out of range");
-    return PFLBM_EINVAL;
-  }
   cudaPointerAttributes pa;
   e = cudaPointerGetAttributes(&pa, fields);
   if (e != cudaSuccess) return cuda_fail("fields pointer", e);
@@ -214,7 +213,7 @@ extern "C" pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, const fl
     return PFLBM_EINVAL;
   }
   double* scratch = nullptr;
-  e = scratch_address(dev, &scratch);
+  e = scratch_address(&scratch);
   if (e != cudaSuccess) return cuda_fail("scratch address", e);
 
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -224,7 +223,8 @@ extern "C" pflbm_status pflbm_field_diagnostics_noalloc(int nx, int ny, const fl
   // the block-completion counter must start at zero
   e = cudaMemsetAsync(scratch + kTicketOff, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail("clear counter", e);
-  k_diag_noalloc<<<nb, kThreads, 0, s>>>(nx, ny, fields, g, scratch);
+  k_diag_noalloc<<<nb, kThreads, 0, s>>>(nx, ny, bc_x == PFLBM_PERIODIC, bc_y == PFLBM_PERIODIC,
+                                         fields, g, scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("launch", e);
   double h[kNRed];

@@ -106,7 +106,7 @@ SIGNATURES = {
     "pflbm_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "pflbm_batch_items": (ctypes.c_longlong, [_vp]),
     "pflbm_batch_destroy": (None, [_vp]),
-    "pflbm_field_diagnostics_noalloc": (_i, [_i, _i, _vp, ctypes.POINTER(pflbm_diag_geom),
+    "pflbm_field_diagnostics_noalloc": (_i, [_i, _i, _i, _i, _vp, ctypes.POINTER(pflbm_diag_geom),
                                          ctypes.POINTER(pflbm_diag), _vp]),
     "pflbm_status_str": (ctypes.c_char_p, [_i]),
     "pflbm_last_error": (ctypes.c_char_p, []),
@@ -247,13 +247,15 @@ def pflbm_bubble_diagnostics(d):
 
 
 def pflbm_field_diagnostics_noalloc(nx: int, ny: int, fields, geom: Optional[pflbm_diag_geom],
-                                    stream=None):
+                                    stream=None, bc_x: int = 0, bc_y: int = 0):
     """FP64 diagnostics of device fields [PFLBM_NFIELDS][ny][nx] through the
     library's static scratch (no allocation); stream is a torch stream, a raw
-    handle or None (legacy default stream).  Returns (status, pflbm_diag)."""
+    handle or None (legacy default stream); bc_x, bc_y the lattice's sides
+    (pflbm_bc values).  Returns (status, pflbm_diag)."""
     out = pflbm_diag()
     handle = getattr(stream, "cuda_stream", stream)
-    st = load().pflbm_field_diagnostics_noalloc(int(nx), int(ny), _ptr(fields),
+    st = load().pflbm_field_diagnostics_noalloc(int(nx), int(ny), int(bc_x), int(bc_y),
+                                                _ptr(fields),
                                                 None if geom is None else ctypes.byref(geom),
                                                 ctypes.byref(out), handle)
     if st not in (0, 4):

@@ -90,11 +90,15 @@ def test_noalloc_diagnostics_size_checks(lib):
     fake = 1 << 20  # never dereferenced: the size checks come first
     out = pflbm.pflbm_diag()
     f = lib.pflbm_field_diagnostics_noalloc
-    assert f(0, 16, fake, None, ctypes.byref(out), None) == 1
-    assert f(16, -1, fake, None, ctypes.byref(out), None) == 1
-    assert f(16, 16, fake, None, None, None) == 1
+    assert f(0, 16, 0, 0, fake, None, ctypes.byref(out), None) == 1
+    assert f(16, -1, 0, 0, fake, None, ctypes.byref(out), None) == 1
+    assert f(16, 16, 0, 0, fake, None, None, None) == 1
+    # boundary kinds: x periodic or free-slip, y periodic or wall
+    assert f(16, 16, pflbm.WALL, 0, fake, None, ctypes.byref(out), None) == 1
+    assert f(16, 16, 0, pflbm.FREESLIP, fake, None, ctypes.byref(out), None) == 1
+    assert "bc_x must be" in lib.pflbm_last_error().decode()
     assert pflbm.NOALLOC_MAX_NODES == 4096 * 2048
-    assert f(4096, 2049, fake, None, ctypes.byref(out), None) == 1
+    assert f(4096, 2049, 0, 0, fake, None, ctypes.byref(out), None) == 1
     msg = lib.pflbm_last_error().decode()
     assert "8392704 nodes" in msg and "at most 8388608 nodes" in msg
     hdr = open(HEADER).read()
