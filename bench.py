@@ -125,6 +125,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# the step kernel each stage mode launches (the dominant kernel of a step)
+KERNEL_OF_STAGE = {"boxes": "k_step_boxes", "gather": "k_step_gather", "march": "k_step_march"}
+
+
 def traffic_record(workload: str, storage: str, stage: str):
     """DRAM bytes per node and step of the step kernel from the committed ncu
     summary of this workload, valid only while the kernel source is unchanged."""
@@ -211,6 +215,24 @@ def max_over_ranks(x: float, ws: int, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, ws: int, device) -> float:
+    """Sum of a per-rank count over the ranks (the value itself on one)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(n: int, rank: int, ws: int):
+    """The contiguous share [lo, hi) of n independent items (the instances of
+    a batch) that rank `rank` of `ws` advances: sizes differ by at most one,
+    the shares are disjoint and cover [0, n)."""
+    return n * rank // ws, n * (rank + 1) // ws
+
+
 def job_glups(ws: int, n_nodes: int, steps: int, seconds: float) -> float:
     """Whole-job throughput of ws independent replicas of n_nodes nodes that
     each advanced `steps` steps in `seconds` (the slowest rank's time)."""
@@ -233,14 +255,16 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2, threads=None):
-    """Oracle steps on the full grid of the workload until `seconds` of CPU
-    work on `threads` OpenMP threads (all host cores by default): returns
-    (GLUPS, steps, threads)."""
+def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2, threads=None, fields=False):
+    """Oracle steps on the full grid of the workload (from the float32 phi0
+    the GPU receives) until `seconds` of CPU work on `threads` OpenMP threads
+    (all host cores by default): returns (GLUPS, steps, threads), and with
+    fields=True also the oracle's fields after its 1 + steps steps."""
     import oracle
     threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
-    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params), case.phi0,
+    s = oracle.Sim(case.nx, case.ny, case.wall_y, oracle.Params(**case.params),
+                   case.phi0.astype(np.float32).astype(np.float64),
                    wall_x=case.meta.get("wall_x", False))
     s.step(1)  # first step separately (first-step flag), untimed
     t0 = time.perf_counter()
@@ -249,7 +273,47 @@ def oracle_sample(case, seconds=10.0, max_steps=400, min_steps=2, threads=None):
         s.step(1)
         n += 1
     dt = time.perf_counter() - t0
-    return case.nx * case.ny * n / dt / 1e9, n, threads
+    out = (case.nx * case.ny * n / dt / 1e9, n, threads)
+    return out + (s.macro(),) if fields else out
+
+
+def pressure_jump(fields, case):
+    """Mean p_h within R/2 of the bubble or drop centre minus its mean beyond
+    R + 3W (the Laplace measurement of Sec. 5.1; distances wrap only across
+    periodic sides)."""
+    m = case.meta
+    xc, yc, R, W = m["xc"], m["yc"], m["R"], case.params["W"]
+    ny, nx = fields["phi"].shape
+    dx = np.abs(np.arange(nx)[None, :] - xc)
+    if not m.get("wall_x", False):
+        dx = np.minimum(dx, nx - dx)
+    dy = np.abs(np.arange(ny)[:, None] - yc)
+    if not case.wall_y:
+        dy = np.minimum(dy, ny - dy)
+    r = np.hypot(dx, dy)
+    ph = np.asarray(fields["p_h"], dtype=np.float64)
+    return float(ph[r <= R / 2].mean() - ph[r >= R + 3 * W].mean())
+
+
+def storage_parity(case, dev, steps, ref):
+    """Errors of the GPU step after `steps` steps from the workload's phi0,
+    with float32, FP16 and BF16 population storage, against the FP64 oracle's
+    fields `ref` after the same steps: max |phi| and |u| errors and the error
+    of the pressure jump relative to the Laplace jump sigma / R."""
+    from paper_2012_14729_gb300 import pflbm
+    out = {"steps": steps}
+    lap = case.params["sigma"] / case.meta["R"]
+    dp_ref = pressure_jump(ref, case)
+    for st in ("fp32", "fp16", "bf16"):
+        d = pflbm.Domain(case.nx, case.ny, wall_y=case.wall_y,
+                         wall_x=case.meta.get("wall_x", False), storage=st, device=dev)
+        d.set_params(**case.params).init_phi(case.phi0.astype(np.float32))
+        d.step(steps)
+        g = d.fields()
+        out[st] = {"phi": float(np.abs(g["phi"] - ref["phi"]).max()),
+                   "u": float(max(np.abs(g["ux"] - ref["ux"]).max(), np.abs(g["uy"] - ref["uy"]).max())),
+                   "dp_over_laplace": abs(pressure_jump(g, case) - dp_ref) / lap}
+    return out
 
 
 def run_reference(args, case):
@@ -373,6 +437,7 @@ def run_ours(args, case):
     stream.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
     e2e = {"value": job_glups(ws, n_nodes, args.steps, e2e_s), "unit": "GLUPS",
+           "steps": args.steps,  # the copies below are amortised over these steps
            "h2d_bytes_per_step": n_nodes * 4 / args.steps,
            "d2h_bytes_per_step": len(pflbm.FIELDS) * n_nodes * 4 / args.steps}
 
@@ -385,7 +450,7 @@ def run_ours(args, case):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tr is None else tr * n_nodes,
                 "algorithmic_bytes": bpl * n_nodes,
-                "kernel": "k_step_boxes" if stage == "boxes" else "k_step_gather"}
+                "kernel": KERNEL_OF_STAGE[stage]}
 
     if rank != 0:
         if ws > 1:
@@ -395,12 +460,15 @@ def run_ours(args, case):
 
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        v, n, thr = oracle_sample(case, seconds=0.75 * args.cpu_seconds)
+        v, n, thr, ref = oracle_sample(case, seconds=0.75 * args.cpu_seconds, fields=True)
         v1, n1, _ = oracle_sample(case, seconds=0.25 * args.cpu_seconds, min_steps=1, threads=1)
         cpu = {"value": v, "unit": "GLUPS", "cores": thr, "kind": "oracle",
                "sample": f"{n} full-grid FP64 oracle steps of {args.workload}",
                "value_1thread": v1, "sample_1thread": f"{n1} steps on one thread",
                "cpu_model": cpu_model()}
+        if "R" in case.meta and "xc" in case.meta:
+            # the GPU path against the oracle's final state of that sample
+            cpu["parity_vs_gpu"] = storage_parity(case, dev, 1 + n, ref)
 
     # the same physics on a grid whose state exceeds L2 (8.4 M nodes, 1.34 GB
     # per step), timed over consecutive steps without flushing
@@ -481,7 +549,7 @@ def main():
     ap.add_argument("--workload", default="bubble_512x1024")
     ap.add_argument("--form", default="STF1")
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp16", "bf16"))
-    ap.add_argument("--stage", default="auto", choices=("auto", "boxes", "gather"))
+    ap.add_argument("--stage", default="auto", choices=("auto", "boxes", "gather", "march"))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -589,10 +657,23 @@ def measure_adjoint(args, consistency=True):
 
 
 def run_batch(args):
-    print(json.dumps(measure_batch(args)), flush=True)
+    """Batched workload; under torchrun each rank advances its own share of
+    the batch's instances (they are independent problems: no data-path
+    collective), the job's time is the slowest rank's."""
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    line = measure_batch(args, ws=ws, rank=rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
-def measure_batch(args, clocks=True):
+def measure_batch(args, clocks=True, ws=1, rank=0):
     """Batched pattern, workload batchN (batch256 is the configuration): N
     drop instances (L from {64, 128, 256, 512}, R in [0.15, 0.35] L, sigma
     log-uniform in [1e-4, 1e-2], force family cycling STF, CPF, PF, CSF),
@@ -606,7 +687,9 @@ def measure_batch(args, clocks=True):
     build.build()
     pflbm.load()
     dev = torch.device("cuda", torch.cuda.current_device())
-    cases = wl.batch_instances(int(args.workload[5:]), seed=0)
+    all_cases = wl.batch_instances(int(args.workload[5:]), seed=0)
+    lo, hi = shard(len(all_cases), rank, ws)
+    cases = all_cases[lo:hi]
     stream = torch.cuda.Stream(dev)
     doms = []
     for c in cases:
@@ -633,7 +716,13 @@ def measure_batch(args, clocks=True):
     if clocks:
         clk = ClockSampler(torch.cuda.current_device())
         clk.__enter__()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
     t_ms = timed(b.step, args.steps)
+    torch.cuda.synchronize()
+    t_ms = max_over_ranks(t_ms, ws, dev)
     if clocks:
         time.sleep(0.15)
         clk.__exit__(None, None, None)
@@ -650,18 +739,21 @@ def measure_batch(args, clocks=True):
     solo(2)
     stream.synchronize()
     k_solo = max(3, args.steps // 10)
-    t_solo = timed(solo, k_solo)
+    t_solo = max_over_ranks(timed(solo, k_solo), ws, dev)
 
+    nodes = int(sum_over_ranks(nodes, ws, dev))  # the whole job's nodes
     ms_per_step = t_ms / args.steps
     value = nodes * args.steps / (t_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     achieved = 160 * nodes / (ms_per_step * 1e-3) / 1e9
     line = {
-        "metric": "GLUPS (coupled f+h step)", "value": value, "unit": "GLUPS", "n_gpus": 1,
+        "metric": "GLUPS (coupled f+h step)", "value": value, "unit": "GLUPS", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        # the batch's instances are split over the ranks: fixed total work
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "instances": len(cases), "nodes": nodes,
+        "config": {"workload": args.workload, "instances": len(all_cases), "nodes": nodes,
+                   "parallelism": f"instances sharded over {ws} rank(s)",
                    "stage": mode, "ctas_per_sm": cps, "tile": f"32x{rows}", "graphs": True,
                    "l2": f"state {160 * nodes / 2**30:.2f} GiB per step (L2 is 129 MB)",
                    "state_status": diag["status"]},

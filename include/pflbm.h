@@ -203,8 +203,15 @@ pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
  *                       shared memory, persistent CTAs (2 per SM)
  *   PFLBM_STAGE_GATHER  L1-cached gathers straight from the planes, one CTA
  *                       per tile (the default)
- * Both compute the same step; results agree to float32 rounding order. */
-enum { PFLBM_STAGE_BOXES = 0, PFLBM_STAGE_GATHER = 1 };
+ *   PFLBM_STAGE_MARCH   persistent CTAs sweep column strips along y; a
+ *                       producer warp stages the pulled population rows
+ *                       ahead into a ring in shared memory, the y halo of
+ *                       phi and its derived fields is kept in row rings.
+ *                       Needs periodic x with nx a multiple of 4 (float32)
+ *                       or 8 (16-bit storage), ny >= 8, no side walls;
+ *                       EINVAL otherwise.  The batch refuses it.
+ * All compute the same step; results agree to float32 rounding order. */
+enum { PFLBM_STAGE_BOXES = 0, PFLBM_STAGE_GATHER = 1, PFLBM_STAGE_MARCH = 2 };
 pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode);
 int pflbm_get_stage_mode(const pflbm_domain* d);
 

@@ -200,6 +200,12 @@ void build_maps(pflbm_domain* d) {
   d->use_tma = ok ? 1 : 0;
 }
 
+// The marching stage mode handles this domain: periodic x in whole 16-byte
+// chunks of the storage type, no side walls, at least 8 rows.
+bool march_ok(const pflbm_domain* d) {
+  return !d->wall_x && d->ny >= 8 && d->nx % (d->storage == kFP32 ? 4 : 8) == 0;
+}
+
 cudaError_t launch_step_mode(const pflbm_domain* d, int mode, const StepArgs& a) {
   const int form = d->par.force;
   switch (d->storage) {
@@ -445,6 +451,11 @@ pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode) {
     set_msg("pflbm_set_stage_mode: side walls are staged by gathers only");
     return PFLBM_EINVAL;
   }
+  if (mode == kMarch && !march_ok(d)) {
+    set_msg("pflbm_set_stage_mode: the march needs nx a multiple of 4 (float32) or 8 "
+            "(16-bit storage) and ny >= 8");
+    return PFLBM_EINVAL;
+  }
   d->mode = mode;
   drop_graph(d);
   return PFLBM_OK;
@@ -471,6 +482,7 @@ pflbm_status pflbm_autotune(pflbm_domain* d, int trial_steps, int* mode_out) {
   int best_mode = d->mode;
   for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
     if (d->wall_x && m != kGather) continue;  // side walls: gathers only
+    if (m == kMarch && !march_ok(d)) continue;
     e = launch_step_mode(d, m, a);  // warm-up (also sets kernel attributes)
     if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
     for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) e = launch_step_mode(d, m, a);
@@ -1151,7 +1163,7 @@ pflbm_status pflbm_batch_set_graphs(pflbm_batch* b, int enable) {
 }
 
 pflbm_status pflbm_batch_set_config(pflbm_batch* b, int mode, int ctas_per_sm) {
-  if (!b || mode < 0 || mode >= kNumModes || ctas_per_sm < 1 ||
+  if (!b || mode < 0 || mode >= kNumBatchModes || ctas_per_sm < 1 ||
       ctas_per_sm > batch_blocks_per_sm(mode))
     return PFLBM_EINVAL;
   if (mode == kBoxes && b->rows != kTY) {
@@ -1263,7 +1275,7 @@ pflbm_status pflbm_batch_autotune(pflbm_batch* b, int trial_steps, int* mode_out
   int best_mode = keep_mode, best_cps = keep_cps, best_rows = keep_rows;
   // candidates: staging mode x tile rows (short tiles with gathers only) x
   // persistent CTAs per SM
-  for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
+  for (int m = 0; m < kNumBatchModes && e == cudaSuccess; ++m) {
     for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
       if (m == kBoxes && kBatchRows[r] != kTY) continue;
       for (int cps = 1; cps <= batch_blocks_per_sm(m) && e == cudaSuccess; ++cps) {

@@ -1,5 +1,5 @@
 // Instantiation of the fused step kernels for fp16 population storage.
-#include "step_kernel.cuh"
+#include "march_kernel.cuh"
 
 namespace pflbm {
 cudaError_t launch_step_fp16(int form, int mode, const StepArgs& a, cudaStream_t s) {

@@ -942,8 +942,14 @@ __global__ void __launch_bounds__(kThreadsGather, 3) k_step_tape(const __grid_co
 
 int num_sms();
 
+// the marching variant (march_kernel.cuh)
+template <int FORM, class ST>
+cudaError_t launch_march(const StepArgs& a, cudaStream_t s);
+
 template <int FORM, class ST>
 cudaError_t launch_form(int mode, const StepArgs& a, cudaStream_t s) {
+  // the macroscopic read-back always takes the tile kernels
+  if (mode == kMarch && !a.macro) return launch_march<FORM, ST>(a, s);
   static bool configured = false;  // per instantiation; attributes are per function
   constexpr int kBoxBytes = 128 + Boxes<ST>::BYTES + Fields<FORM>::BYTES;
   constexpr int kGatherBytes = Fields<FORM>::BYTES;

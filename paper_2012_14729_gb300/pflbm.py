@@ -193,7 +193,7 @@ def pflbm_set_tma(d, enable: bool):
     _check(load().pflbm_set_tma(d, int(bool(enable))), "pflbm_set_tma")
 
 
-STAGE_MODES = {"boxes": 0, "gather": 1}
+STAGE_MODES = {"boxes": 0, "gather": 1, "march": 2}
 
 
 def pflbm_set_stage_mode(d, mode: int):
@@ -468,6 +468,10 @@ class Domain:
     def stage_mode(self, mode) -> "Domain":
         pflbm_set_stage_mode(self.h, STAGE_MODES.get(mode, mode))
         return self
+
+    def stage(self) -> str:
+        """Name of the stage mode the step kernel uses."""
+        return {v: k for k, v in STAGE_MODES.items()}[pflbm_get_stage_mode(self.h)]
 
     def autotune(self, trial_steps: int = 20) -> str:
         m = pflbm_autotune(self.h, trial_steps)

@@ -173,7 +173,8 @@ def capillary_bubble(kind="bubble", form="STF1", nx=512, ny=1024, W=5.0,
     phi0 = np.clip(phi0 + noise(nx, ny, noise_amp, seed), -1.0, 1.0)
     p = dict(sigma=sigma, W=W, M=M, tau_h=1.0, rho1=1.0, rho2=1.0 / ratio,
              nu1=nu1, nu2=nu1 / visc_ratio, gx=0.0, gy=gy, form=form)
-    return Case(f"capillary_{kind}", nx, ny, True, p, phi0, 50000, {"R": R})
+    meta = {"R": R} if kind == "wave" else {"R": R, "xc": nx / 2, "yc": ny / 4}
+    return Case(f"capillary_{kind}", nx, ny, True, p, phi0, 50000, meta)
 
 
 UG_PHYS = math.sqrt(2 * 0.25 * 0.98)  # reference velocity sqrt(2 R g) of Sec. 5.4, m/s

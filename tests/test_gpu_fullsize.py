@@ -85,7 +85,7 @@ def _check_patches(orc, case, state, patches, wall_x_patch=False):
     return worst
 
 
-@pytest.mark.parametrize("stage", ["gather", "boxes"])
+@pytest.mark.parametrize("stage", ["gather", "boxes", "march"])
 def test_bench_workload_512x1024_sampled(pf, orc, stage):
     c = wl.capillary_bubble("bubble")
     state = _run(pf, c, stage, 40, False)
@@ -96,6 +96,17 @@ def test_bench_workload_512x1024_sampled(pf, orc, stage):
                 (c.ny // 4 - P // 2, c.nx // 2 - P // 2, "interface")]
     worst = _check_patches(orc, c, state, patches)
     print(f"{stage}: largest error / scale {worst:.2e}")
+
+
+def test_l2_exceeding_workload_2048x4096_march_sampled(pf, orc):
+    """The bench's L2-exceeding point (the same physics on 2048 x 4096, walls
+    at bottom and top, periodic x) in the march mode."""
+    c = wl.capillary_bubble("bubble", nx=2048, ny=4096)
+    state = _run(pf, c, "march", 20, False)
+    patches = [(1000, 1000, "interior"), (0, 64 * 7 - P // 2, "bottom"), (c.ny - P, 1500, "top"),
+               (2000, c.nx - P // 2, "seam"), (c.ny // 4 - 64 - P // 2, c.nx // 2 - P // 2, "interface")]
+    worst = _check_patches(orc, c, state, patches)
+    print(f"march 2048x4096: largest error / scale {worst:.2e}")
 
 
 def test_side_wall_workload_2048x4096_sampled(pf, orc):

@@ -55,3 +55,46 @@ def test_one_rank_is_the_identity():
     import bench
     assert bench.max_over_ranks(3.25, 1, "cpu") == 3.25
     assert bench.job_glups(1, 1000, 10, 1e-3) == pytest.approx(1e-2)
+
+
+def _shard_rank(rank, ws, port, n, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        lo, hi = bench.shard(n, rank, ws)
+        total = bench.sum_over_ranks(hi - lo, ws, "cpu")
+        shares = [None] * ws
+        dist.all_gather_object(shares, (lo, hi))
+        q.put((rank, (lo, hi), total, shares))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws,n", [(2, 256), (2, 7), (3, 256)])
+def test_batch_instances_are_sharded_disjoint_and_covering(ws, n):
+    """A batch's instances are independent problems: under torchrun each rank
+    advances its own contiguous share of them (no data-path collective), the
+    shares are disjoint and together cover every instance, and the job's node
+    count is the sum over the ranks."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, ws, port, n, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    covered = []
+    for rank, (lo, hi), total, shares in res:
+        assert shares == [r[1] for r in res]  # every rank sees the same split
+        assert total == n
+        assert hi - lo in (n // ws, n // ws + 1)
+        covered.extend(range(lo, hi))
+    assert covered == list(range(n))
