@@ -203,10 +203,11 @@ pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
  *                       shared memory, persistent CTAs (2 per SM)
  *   PFLBM_STAGE_GATHER  L1-cached gathers straight from the planes, one CTA
  *                       per tile (the default)
- *   PFLBM_STAGE_MARCH   persistent CTAs sweep column strips along y; a
- *                       producer warp stages the pulled population rows
- *                       ahead into a ring in shared memory, the y halo of
- *                       phi and its derived fields is kept in row rings.
+ *   PFLBM_STAGE_MARCH   persistent CTAs sweep column strips along y; the
+ *                       pulled population rows are copied two iterations
+ *                       ahead into a ring in shared memory (cp.async), the
+ *                       y halo of phi and its derived fields is kept in row
+ *                       rings.
  *                       Needs periodic x with nx a multiple of 4 (float32)
  *                       or 8 (16-bit storage), ny >= 8, no side walls;
  *                       EINVAL otherwise.  The batch refuses it.

@@ -88,10 +88,10 @@ constexpr int kShortRows = 8;
 //            persistent grid of two 512-thread CTAs per SM, each walking tiles
 //   kGather  direct L1-cached gathers from global memory; one 256-thread CTA
 //            per tile, four CTAs per SM
-//   kMarch   column strips swept along y by persistent CTAs, population rows
-//            staged ahead by a producer warp (march_kernel.cuh); single
-//            domains only, periodic x with nx a multiple of the 16-byte
-//            chunk, no side walls
+//   kMarch   column strips swept along y by persistent CTAs, the pulled
+//            population rows staged ahead into a shared-memory ring by
+//            cp.async (march_kernel.cuh); single domains only, periodic x
+//            with nx a multiple of the 16-byte chunk, no side walls
 enum StageMode { kBoxes = 0, kGather = 1, kMarch = 2, kNumModes = 3 };
 constexpr int kNumBatchModes = 2;  // the batch stages by boxes or gathers
 constexpr int kThreadsBoxes = 512;

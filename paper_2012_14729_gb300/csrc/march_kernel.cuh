@@ -3,15 +3,16 @@
 // in step_kernel.cuh, organised as a sweep along y instead of halo tiles.
 //
 // A persistent CTA owns contiguous runs of rows of a kMW-wide column strip
-// and walks down them kMR rows per iteration.  Its warps are specialised:
-//   - one producer warp copies, for every node row the sweep reaches, the 18
-//     pulled population rows of the strip (each plane's row shifted by -c_iy,
-//     all columns of the strip plus a 16-byte aligned halo) and the row of
-//     (phi u)^{t-1} into a ring of row slots in shared memory, with 16-byte
-//     cp.async copies that complete on the slot's mbarrier.  Periodic seams
-//     and wall ghost rows are resolved in the copy (chunk by chunk), so the
-//     compute warps never wrap an index;
-//   - eight compute warps run, per iteration with output rows [y, y + kMR),
+// and walks down them kMR rows per iteration.  Per iteration with output
+// rows [y, y + kMR) its threads
+//   - issue 16-byte cp.async copies of the population rows the next
+//     iteration needs into a ring of row slots in shared memory: for every
+//     node row, the 18 pulled population rows of the strip (each plane's row
+//     shifted by -c_iy, the strip's columns plus a 16-byte aligned halo) and
+//     the row of (phi u)^{t-1}.  Periodic seams are resolved chunk by chunk
+//     and wall ghost rows are ordinary storage rows, so no stage below wraps
+//     an index; the copies land while this iteration computes;
+//   - run
 //       A  phi = sum_i h_i                    on rows [y+3, y+kMR+3), strip+3
 //       B  grad phi, lap phi, mu, form fields on rows [y+2, y+kMR+2), strip+2
 //          (Eqs. ICS-1st, ICS-sec, chemical_potential)
@@ -39,20 +40,9 @@ namespace pflbm {
 constexpr int kMW = 64;                    // strip width (output columns)
 constexpr int kMR = 4;                     // output rows per iteration
 constexpr int kMRing = 8;                  // rows of the field rings (power of 2)
-constexpr int kMCompute = 256;             // compute threads (8 warps)
-constexpr int kMThreads = kMCompute + 32;  // and one producer warp
+constexpr int kMThreads = 256;             // threads per CTA (8 warps)
 constexpr int kMBlocks = 2;                // CTAs per SM
 
-// mbarrier helpers beyond those of step_kernel.cuh
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-// arrive on `bar` when this thread's earlier cp.async copies have completed
-// (the barrier's expected count includes this arrival)
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
-               : "memory");
-}
 // 16-byte asynchronous copy global -> shared, bypassing L1; zero-filled when
 // !valid (nothing is read then)
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
@@ -60,26 +50,20 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
                "r"(valid ? 16 : 0)
                : "memory");
 }
-// barrier among the compute warps only (named barrier 1), with an OR of `v`
-__device__ __forceinline__ int compute_sync_or(int v) {
-  int r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n"
-      " bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}"
-      : "=r"(r)
-      : "r"(v), "n"(kMCompute)
-      : "memory");
-  return r;
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void compute_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kMCompute) : "memory");
+// wait until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void cp_async_wait_one() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
 // Geometry of one row slot of the population ring for storage ST: h_0, then
 // h_1..h_8 and f_0..f_8 (the "uniform" planes, in the storage type), then the
 // two rows of (phi u)^{t-1}.  Column b of a population plane holds global
 // column x0 - XP + b (XP: 16 bytes of halo), pulled for the node of the slot's
-// row, i.e. storage row (row - c_iy) + 1.
+// row, i.e. storage row (row - c_iy) + 1.  Every plane row starts on a
+// 16-byte boundary and spans a whole number of 16-byte chunks.
 template <class ST>
 struct MarchSlot {
   using T = typename ST::T;
@@ -87,18 +71,21 @@ struct MarchSlot {
   static constexpr int XP = 16 / EB;          // halo columns of a uniform plane
   static constexpr int PW = kMW + 2 * XP;     // columns of a uniform plane
   static constexpr int CE = 16 / EB;          // elements per 16-byte chunk
-  static constexpr int NCH = PW / CE;         // chunks per uniform plane row
   static constexpr int XP0 = ST::kSplitH0 ? 4 : XP;  // h_0 (float32 when split)
   static constexpr int PW0 = kMW + 2 * XP0;
-  static constexpr int CE0 = ST::kSplitH0 ? 4 : CE;  // elements of h_0 per chunk
-  static constexpr int NCH0 = PW0 / CE0;             // chunks of h_0
   static constexpr int H0B = ST::kSplitH0 ? PW0 * 4 : PW * EB;
   static constexpr int UB = PW * EB;          // bytes of a uniform plane row
   static constexpr int OFF_U = H0B;           // h_1..h_8, f_0..f_8
   static constexpr int OFF_PU = OFF_U + 17 * UB;
-  static constexpr int NCHPU = kMW / 4;       // chunks of a (phi u) row
+  static constexpr int CE0 = ST::kSplitH0 ? 4 : CE;  // elements of h_0 per chunk
+  static constexpr int NCH0 = PW0 / CE0;             // 16-byte chunks of a row of h_0
+  static constexpr int NCHU = PW / CE;               // ... of a uniform plane
+  static constexpr int NCHP = kMW / 4;               // ... of a (phi u) row
+  static constexpr int ROWCH = NCH0 + 17 * NCHU + 2 * NCHP;  // chunks of a node row
   static constexpr int BYTES = (OFF_PU + 2 * kMW * 4 + 127) / 128 * 128;
-  static constexpr int SLOTS = EB == 4 ? 14 : 20;
+  // rows in use in an iteration (kMR + 3) and the two next iterations' new
+  // rows in flight (2 kMR)
+  static constexpr int SLOTS = 3 * kMR + 3;
   static_assert(PW % CE == 0 && H0B % 16 == 0 && UB % 16 == 0, "16-byte chunks");
   // uniform plane u: h_{u+1} for u < 8, f_{u-8} otherwise
   __device__ static int uoff(int u) { return OFF_U + u * UB; }
@@ -124,8 +111,7 @@ template <int FORM, class ST>
 struct MarchSmem {
   using G = MarchSlot<ST>;
   using F = MarchFields<FORM>;
-  static constexpr int OFF_BAR = 0;                       // full[SLOTS], empty[SLOTS]
-  static constexpr int OFF_RING = pad128(2 * G::SLOTS * 8);
+  static constexpr int OFF_RING = 0;
   static constexpr int OFF_FIELDS = OFF_RING + G::SLOTS * G::BYTES;
   static constexpr int BYTES = OFF_FIELDS + F::BYTES;
   static_assert(BYTES <= 113 * 1024, "two CTAs per SM");
@@ -154,55 +140,75 @@ __device__ __forceinline__ float ics3_dy_of(const Fn& a, int c) {
 
 __device__ __forceinline__ int ring_row(int r) { return r & (kMRing - 1); }
 
-// Node row v of the strip at x0 into a row slot (all 32 lanes of the
-// producer warp).  Population i of node row v is pulled from storage row
-// (v - c_iy) + 1 (walls: the ghost rows hold the bounced populations; rows
-// beyond a wall are not pulled and are zero-filled); periodic y wraps v - c_iy;
-// columns wrap periodically chunk by chunk (nx is a multiple of the chunk).
+// The 16-byte chunks of a node row that one thread copies (at most two: a row
+// has ROWCH chunks, the CTA kMThreads threads), fixed for a strip: chunk k
+// reads storage row r of its plane at base[k] + r * pitch[k] and lands at
+// byte dst[k] of the row's slot.  Population chunks read storage row
+// (v - cy) + 1 for node row v; (phi u) chunks read row v (no ghost rows).
+struct FillPlan {
+  const unsigned char* base[2];
+  int pitch[2], dst[2], cy[2], pu[2];
+  int n;
+};
+
 template <class ST>
-__device__ __forceinline__ void march_fill_row(const StepArgs& a, unsigned char* slot, int x0,
-                                               int v, int lane) {
+__device__ __forceinline__ FillPlan march_fill_plan(const StepArgs& a, int x0) {
   using G = MarchSlot<ST>;
   using T = typename ST::T;
   const Lattice& L = a.L;
-  const bool pull = !L.wall || (v >= 0 && v < L.ny);
-  const auto srow = [&](int cy) { return L.wall ? v - cy + 1 : wrap(v - cy, L.ny) + 1; };
-  {  // h_0
-    const int sr = srow(0);
-    const float* base = ST::kSplitH0 ? a.h0_in : reinterpret_cast<const float*>(a.h_in);
-    for (int j = lane; j < G::NCH0; j += 32) {
-      const int gx = wrap(x0 - G::XP0 + j * G::CE0, L.nx);
-      const float* src = pull ? base + (size_t)sr * L.nx + gx : base;
-      cp_async16(slot + j * 16, src, pull);
+  FillPlan pl;
+  pl.n = 0;
+  for (int c0 = threadIdx.x; c0 < G::ROWCH; c0 += kMThreads) {
+    const int k = pl.n++;
+    int c = c0;
+    if (c < G::NCH0) {  // h_0
+      const float* b = ST::kSplitH0 ? a.h0_in : reinterpret_cast<const float*>(a.h_in);
+      pl.base[k] = reinterpret_cast<const unsigned char*>(b + wrap(x0 - G::XP0 + c * G::CE0, L.nx));
+      pl.pitch[k] = L.nx * 4;
+      pl.dst[k] = c * 16;
+      pl.cy[k] = 0;
+      pl.pu[k] = 0;
+    } else if ((c -= G::NCH0) < 17 * G::NCHU) {  // h_1..h_8, f_0..f_8
+      const int u = c / G::NCHU, j = c - u * G::NCHU;
+      const int i = u < 8 ? u + 1 : u - 8;
+      const T* b = u < 8 ? reinterpret_cast<const T*>(a.h_in) +
+                               (size_t)(ST::kSplitH0 ? i - 1 : i) * L.plane
+                         : reinterpret_cast<const T*>(a.f_in) + (size_t)i * L.plane;
+      pl.base[k] = reinterpret_cast<const unsigned char*>(b + wrap(x0 - G::XP + j * G::CE, L.nx));
+      pl.pitch[k] = L.nx * G::EB;
+      pl.dst[k] = G::uoff(u) + j * 16;
+      pl.cy[k] = qcy(i);
+      pl.pu[k] = 0;
+    } else {  // (phi u)^{t-1}
+      c -= 17 * G::NCHU;
+      const int comp = c / G::NCHP, j = c - comp * G::NCHP;
+      pl.base[k] = reinterpret_cast<const unsigned char*>(
+          a.phiu + (size_t)comp * L.nx * L.ny + wrap(x0 + 4 * j, L.nx));
+      pl.pitch[k] = L.nx * 4;
+      pl.dst[k] = G::OFF_PU + comp * kMW * 4 + j * 16;
+      pl.cy[k] = 0;
+      pl.pu[k] = 1;
     }
   }
-  for (int e = lane; e < 17 * G::NCH; e += 32) {  // h_1..h_8, f_0..f_8
-    const int u = e / G::NCH, j = e - u * G::NCH;
-    const int i = u < 8 ? u + 1 : u - 8;
-    const T* base = u < 8 ? reinterpret_cast<const T*>(a.h_in) +
-                                (size_t)(ST::kSplitH0 ? i - 1 : i) * L.plane
-                          : reinterpret_cast<const T*>(a.f_in) + (size_t)i * L.plane;
-    const int gx = wrap(x0 - G::XP + j * G::CE, L.nx);
-    const T* src = pull ? base + (size_t)srow(qcy(i)) * L.nx + gx : base;
-    cp_async16(slot + G::uoff(u) + j * 16, src, pull);
-  }
-  // (phi u)^{t-1}: rows [0, ny) without ghost rows, x and y components
-  const bool inside = v >= 0 && v < L.ny;
-  const int vr = inside ? v : (L.wall ? 0 : wrap(v, L.ny));
-  const size_t nn = (size_t)L.nx * L.ny;
-  for (int e = lane; e < 2 * G::NCHPU; e += 32) {
-    const int comp = e / G::NCHPU, j = e - comp * G::NCHPU;
-    const int gx = wrap(x0 + 4 * j, L.nx);
-    cp_async16(slot + G::OFF_PU + comp * kMW * 4 + j * 16,
-               a.phiu + comp * nn + (size_t)vr * L.nx + gx, inside || !L.wall);
-  }
+  return pl;
 }
 
-// Bounded mbarrier wait of one thread; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long n = 0; !mbar_try_wait(bar, parity);)
-    if (++n > kWaitLimit) return false;
-  return true;
+// Issue this thread's copies of node row v into `slot`.  Population i of
+// node row v is pulled from storage row (v - c_iy) + 1 (walls: the ghost rows
+// hold the bounced populations; rows beyond a wall are not pulled and read as
+// zero); periodic y wraps v - c_iy.
+__device__ __forceinline__ void march_fill_row(const FillPlan& pl, const Lattice& L,
+                                               unsigned char* slot, int v) {
+  const bool inside = v >= 0 && v < L.ny;
+  const bool valid = inside || !L.wall;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (k >= pl.n) break;
+    int r = v - pl.cy[k];
+    if (!L.wall && (r < 0 || r >= L.ny)) r = wrap(r, L.ny);
+    r += 1 - pl.pu[k];  // storage rows of the population planes start at the ghost row
+    cp_async16(slot + pl.dst[k], pl.base[k] + (valid ? (size_t)r * pl.pitch[k] : 0), valid);
+  }
 }
 
 template <int FORM, class ST>
@@ -215,8 +221,6 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
   constexpr int W3 = F::W3, W2 = F::W2, W1 = F::W1;
   constexpr bool kScaled = ST::kSplitH0;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::OFF_BAR);
-  uint64_t* empty = full + G::SLOTS;
   unsigned char* ring = sm + S::OFF_RING;
   float* sPhi = reinterpret_cast<float*>(sm + S::OFF_FIELDS + F::OFF_PHI);
   float* s2 = reinterpret_cast<float*>(sm + S::OFF_FIELDS + F::OFF_S2);
@@ -225,52 +229,14 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
   const Phys& P = a.p;
   const int tid = threadIdx.x;
 
-  if (tid == 0) {
-    for (int k = 0; k < G::SLOTS; ++k) {
-      mbar_init(&full[k], 32);                 // one cp.async arrival per producer lane
-      mbar_init(&empty[k], kMCompute / 32);    // one arrival per compute warp
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-
   // this CTA's share: (strip, row) pairs [lo, hi) in strip-major order
   const int nstrips = (L.nx + kMW - 1) / kMW;
   const long long total = (long long)nstrips * L.ny;
   const long long lo = total * blockIdx.x / gridDim.x;
   const long long hi = total * (blockIdx.x + 1) / gridDim.x;
 
-  if (tid >= kMCompute) {
-    // ---- producer warp: fill row slots in the order the sweep uses them ----
-    const int lane = tid - kMCompute;
-    long long seq = 0;
-    for (long long w = lo; w < hi;) {
-      const int strip = (int)(w / L.ny);
-      const long long wend = hi < (long long)(strip + 1) * L.ny ? hi : (long long)(strip + 1) * L.ny;
-      const int ya = (int)(w - (long long)strip * L.ny), yb = (int)(wend - (long long)strip * L.ny);
-      const int vend = ya + (yb - ya + kMR - 1) / kMR * kMR + 3;
-      for (int v = ya - 3; v < vend; ++v, ++seq) {
-        const int slot = (int)(seq % G::SLOTS);
-        const uint32_t ph = (uint32_t)((seq / G::SLOTS) & 1);
-        // the slot's previous row released by every compute warp
-        const bool ok = mbar_wait_bounded(&empty[slot], ph ^ 1u);
-        if (__any_sync(0xffffffffu, !ok)) {
-          if (lane == 0) atomicOr(a.err, 1);
-          cp_async_wait_all();
-          return;
-        }
-        march_fill_row<ST>(a, ring + slot * G::BYTES, strip * kMW, v, lane);
-        cp_async_arrive_noinc(&full[slot]);
-      }
-      w = wend;
-    }
-    cp_async_wait_all();
-    return;
-  }
-
-  // ---- compute warps ----------------------------------------------------------
   const int nn = L.nx * L.ny;
-  long long seq_base = 0;  // sequence index of the current segment's first row
+  int seq_base = 0;  // sequence index (ring position) of the segment's first row
   for (long long w = lo; w < hi;) {
     const int strip = (int)(w / L.ny);
     const long long wend = hi < (long long)(strip + 1) * L.ny ? hi : (long long)(strip + 1) * L.ny;
@@ -279,22 +245,18 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     const int vend = ya + niter * kMR + 3;
     const int x0 = strip * kMW;
     const auto seq_of = [&](int v) { return seq_base + (v - (ya - 3)); };
+    const FillPlan plan = march_fill_plan<ST>(a, x0);
+    const auto fill = [&](int v0, int v1) {  // rows of [v0, v1) that exist
+      if (v1 > vend) v1 = vend;
+      for (int v = v0; v < v1; ++v)
+        march_fill_row(plan, L, ring + (seq_of(v) % G::SLOTS) * G::BYTES, v);
+      cp_async_commit();
+    };
     const auto slot_ptr = [&](int v) -> const unsigned char* {
-      return ring + (int)(seq_of(v) % G::SLOTS) * G::BYTES;
+      return ring + (seq_of(v) % G::SLOTS) * G::BYTES;
     };
-    int timed_out = 0;
-    const auto wait_rows = [&](int v0, int v1) {
-      for (int v = v0; v < v1; ++v) {
-        const long long q = seq_of(v);
-        if (!mbar_wait_bounded(&full[q % G::SLOTS], (uint32_t)((q / G::SLOTS) & 1))) timed_out = 1;
-      }
-    };
-    const auto release_rows = [&](int v0, int v1) {
-      __syncwarp();
-      if ((tid & 31) == 0)
-        for (int v = v0; v < v1; ++v) mbar_arrive(&empty[seq_of(v) % G::SLOTS]);
-    };
-    // population i of a slot at strip column b (node offset from x0)
+    // population i of a slot at strip column b (node offset from x0), in the
+    // storage scale
     const auto hpop = [&](const unsigned char* sl, int i, int b) -> float {
       if (i == 0) return reinterpret_cast<const float*>(sl)[b + G::XP0];
       return ST::raw(reinterpret_cast<const T*>(sl + G::uoff(i - 1))[b + G::XP - qcx(i)]);
@@ -309,7 +271,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     // A: phi on rows [r0, r1), strip columns -3 .. kMW + 2
     const auto stageA = [&](int r0, int r1) {
       const int n = (r1 - r0) * W3;
-      for (int k = tid; k < n; k += kMCompute) {
+      for (int k = tid; k < n; k += kMThreads) {
         const int rr = k / W3, c = k - rr * W3;
         const int v = r0 + rr, b = c - 3;
         const unsigned char* sl = slot_ptr(v);
@@ -323,7 +285,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     // beyond a wall whose mirror row is still in the ring
     const auto mirror_phi = [&](int r0, int r1) {
       const int n = (r1 - r0) * W3;
-      for (int k = tid; k < n; k += kMCompute) {
+      for (int k = tid; k < n; k += kMThreads) {
         const int rr = k / W3, c = k - rr * W3;
         const int v = r0 + rr;
         if (v >= 0 && v < L.ny) continue;
@@ -334,7 +296,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     // B: level-1 fields on rows [r0, r1), strip columns -2 .. kMW + 1
     const auto stageB = [&](int r0, int r1) {
       const int n = (r1 - r0) * W2;
-      for (int k = tid; k < n; k += kMCompute) {
+      for (int k = tid; k < n; k += kMThreads) {
         const int rr = k / W2, c = k - rr * W2;
         const int v = r0 + rr, cc = c + 1;
         const float* pm = phi_row(v - 1);
@@ -362,7 +324,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     // C: force, rho, u, phi u on rows [r0, r1), strip columns -1 .. kMW
     const auto stageC = [&](int r0, int r1) {
       const int n = (r1 - r0) * W1;
-      for (int k = tid; k < n; k += kMCompute) {
+      for (int k = tid; k < n; k += kMThreads) {
         const int rr = k / W1, c = k - rr * W1;
         const int v = r0 + rr, b = c - 1, c2 = c + 1;
         const float phi = phi_row(v)[c + 2];
@@ -432,7 +394,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     };
     // walls: ghost of phi u beyond a wall, phi (2 u_w - u) of the mirrored node
     const auto ghost_phiu = [&](int r0, int r1) {
-      for (int c = tid; c < W1; c += kMCompute) {
+      for (int c = tid; c < W1; c += kMThreads) {
         if (r0 <= -1 && -1 < r1) {
           const float pm = phi_row(0)[c + 2];
           s1_row(F::PUX, -1)[c] = pm * (2.0f * P.uwb - s1_row(F::UX, 0)[c]);
@@ -448,7 +410,7 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     // D: collide and store the nodes of rows [r0, r1)
     const auto stageD = [&](int r0, int r1) {
       const int n = (r1 - r0) * kMW;
-      for (int k = tid; k < n; k += kMCompute) {
+      for (int k = tid; k < n; k += kMThreads) {
         const int rr = k / kMW, c = k - rr * kMW;
         const int gy = r0 + rr, gx = x0 + c;
         if (gx >= L.nx) continue;
@@ -579,61 +541,59 @@ __global__ void __launch_bounds__(kMThreads, kMBlocks)
     };
     const auto outside = [&](int r0, int r1) { return L.wall && (r0 < 0 || r1 > L.ny); };
 
-    // prologue: phi on [ya-3, ya+3), level-1 on [ya-2, ya+2), level-2 on [ya-1, ya+1)
-    wait_rows(ya - 3, ya + 3);
+    // prologue: the rows of the prologue and of the first iteration, then
+    // phi on [ya-3, ya+3), level-1 on [ya-2, ya+2), level-2 on [ya-1, ya+1)
+    fill(ya - 3, ya + kMR + 3);
+    fill(ya + kMR + 3, ya + 2 * kMR + 3);  // the second iteration's new rows
+    cp_async_wait_one();
+    __syncthreads();
     stageA(ya - 3, ya + 3);
-    if (compute_sync_or(timed_out)) {
-      if (tid == 0) atomicOr(a.err, 1);
-      return;
-    }
+    __syncthreads();
     if (outside(ya - 3, ya + 3)) {
       mirror_phi(ya - 3, ya + 3);
-      compute_sync();
+      __syncthreads();
     }
     stageB(ya - 2, ya + 2);
-    compute_sync();
+    __syncthreads();
     stageC(ya - 1, ya + 1);
-    compute_sync();
+    __syncthreads();
     if (outside(ya - 1, ya + 1)) {
       ghost_phiu(ya - 1, ya + 1);
-      compute_sync();
+      __syncthreads();
     }
-    release_rows(ya - 3, ya);
     for (int it = 0; it < niter; ++it) {
       const int y = ya + it * kMR;
-      wait_rows(y + 3, y + kMR + 3);
-      stageA(y + 3, y + kMR + 3);
-      if (compute_sync_or(timed_out)) {
-        if (tid == 0) atomicOr(a.err, 1);
-        return;
+      // this iteration's rows landed (every group but the newest); then the
+      // rows of the iteration after the next, into slots last used by rows
+      // that every thread has finished with (the barrier ending the last
+      // iteration)
+      if (it > 0) {
+        cp_async_wait_one();
+        __syncthreads();
       }
+      fill(y + 2 * kMR + 3, y + 3 * kMR + 3);
+      stageA(y + 3, y + kMR + 3);
+      __syncthreads();
       if (outside(y + 3, y + kMR + 3)) {
         mirror_phi(y + 3, y + kMR + 3);
-        compute_sync();
+        __syncthreads();
       }
       stageB(y + 2, y + kMR + 2);
-      compute_sync();
+      __syncthreads();
       stageC(y + 1, y + kMR + 1);
-      compute_sync();
+      __syncthreads();
       if (outside(y + 1, y + kMR + 1)) {
         ghost_phiu(y + 1, y + kMR + 1);
-        compute_sync();
+        __syncthreads();
       }
       stageD(y, y + kMR < yb ? y + kMR : yb);
-      release_rows(y, it == niter - 1 ? vend : y + kMR);
-      compute_sync();
+      __syncthreads();
     }
+    cp_async_wait_all();
+    __syncthreads();
     seq_base += vend - (ya - 3);
     w = wend;
   }
-}
-
-// The march handles this lattice (periodic x in whole 16-byte chunks, no
-// side walls).
-template <class ST>
-inline bool march_supported(const Lattice& L) {
-  using G = MarchSlot<ST>;
-  return !L.wall_x && L.nx % G::CE == 0 && L.nx % 4 == 0 && L.ny >= 8;
 }
 
 template <int FORM, class ST>

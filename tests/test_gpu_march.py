@@ -48,16 +48,16 @@ def _errs(g, o):
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_march_stationary_drop_1000_steps(pf, orc, form):
+def test_march_stationary_drop_1000_steps(pf, orc, form, march="march"):
     c = wl.stationary_drop(form)
-    d = _gpu(pf, c.nx, c.ny, False, c.params, c.phi0, 1000, "march")
-    assert d.stage() == "march"
+    d = _gpu(pf, c.nx, c.ny, False, c.params, c.phi0, 1000, march)
+    assert d.stage() == march
     e_phi, e_u = _errs(d.fields(), _oracle(orc, c.nx, c.ny, False, c.params, c.phi0, 1000))
     assert e_phi <= TOL_PHI and e_u <= TOL_U, (e_phi, e_u)
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_march_walls_ragged(pf, orc, form):
+def test_march_walls_ragged(pf, orc, form, march="march"):
     """100 x 37: a strip of 36 columns after one of 64, rows not a multiple
     of the 4 per iteration; walls moving at -/+0.01, gravity, density ratio
     4, viscosity ratio 2, a drop near the bottom wall."""
@@ -65,7 +65,7 @@ def test_march_walls_ragged(pf, orc, form):
     phi0 = wl.drop(nx, ny, 9.0, 4.0, xc=61.3, yc=11.2, periodic_y=False)
     p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.25, nu1=0.1, nu2=0.2,
              gy=-1e-5, uw_bottom=-0.01, uw_top=0.01, form=form)
-    d = _gpu(pf, nx, ny, True, p, phi0, 300, "march")
+    d = _gpu(pf, nx, ny, True, p, phi0, 300, march)
     e_phi, e_u = _errs(d.fields(), _oracle(orc, nx, ny, True, p, phi0, 300))
     assert e_phi <= TOL_PHI and e_u <= TOL_U, (e_phi, e_u)
 
@@ -83,20 +83,22 @@ def _case(wall):
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("wall", [False, True])
 @pytest.mark.parametrize("form", ["STF1", "CPF1", "PF2", "CSF2"])
-def test_march_equals_gather(pf, storage, wall, form):
+def test_march_equals_gather(pf, storage, wall, form, march="march"):
     """Same populations as the gather mode after 60 steps, to float32
     rounding (the two kernels are compiled separately and may contract
-    multiply-adds differently); the largest difference is printed."""
+    multiply-adds differently; a 16-bit value that lands on the other side of
+    a rounding boundary differs by one unit in the last place, 2^-11 of its
+    scale for FP16 and 2^-8 for BF16); the largest difference is printed."""
     nx, ny, phi0, p = _case(wall)
     p["form"] = form
-    out = [_gpu(pf, nx, ny, wall, p, phi0, 60, st, storage).populations() for st in ("gather", "march")]
+    out = [_gpu(pf, nx, ny, wall, p, phi0, 60, st, storage).populations() for st in ("gather", march)]
     worst = 0.0
     for a, b in zip(out[0], out[1]):
         scale = float(np.abs(a).max())
         diff = float(np.abs(a.astype(np.float64) - b).max())
         worst = max(worst, diff / scale)
     print(f"MARCH=GATHER {form} {storage} walls={wall}: largest difference / scale {worst:.2e}")
-    assert worst <= (2e-5 if storage == "fp32" else 2e-3), worst
+    assert worst <= {"fp32": 2e-5, "fp16": 2e-3, "bf16": 1e-2}[storage], worst
 
 
 @pytest.mark.parametrize("wall", [False, True])
@@ -111,7 +113,7 @@ def test_march_16bit_against_oracle(pf, orc, storage, tol_phi, tol_u, wall):
 
 @pytest.mark.parametrize("shape,wall", [((192, 100), False), ((64, 600), True), ((320, 44), True),
                                         ((48, 8), False)])
-def test_march_work_split(pf, shape, wall):
+def test_march_work_split(pf, shape, wall, march="march"):
     """CTA shares that start and end inside strips and span strip boundaries
     (several segments per CTA), a one-strip lattice narrower than the strip,
     the smallest height the mode accepts: equal to the gather mode."""
@@ -120,7 +122,7 @@ def test_march_work_split(pf, shape, wall):
     p = dict(sigma=0.01, W=4.0, M=0.1, rho1=1.0, rho2=0.5, nu1=0.1, nu2=0.1, form="CSF1",
              uw_top=0.01 if wall else 0.0, gy=-1e-5)
     a = _gpu(pf, nx, ny, wall, p, phi0, 40, "gather").populations()
-    b = _gpu(pf, nx, ny, wall, p, phi0, 40, "march").populations()
+    b = _gpu(pf, nx, ny, wall, p, phi0, 40, march).populations()
     for x, y in zip(a, b):
         assert float(np.abs(x.astype(np.float64) - y).max()) <= 2e-5 * float(np.abs(x).max())
 
