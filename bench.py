@@ -129,15 +129,27 @@ def measured_peaks():
 KERNEL_OF_STAGE = {"boxes": "k_step_boxes", "gather": "k_step_gather", "march": "k_step_march"}
 
 
+# the sources the step kernels are compiled from
+KERNEL_SOURCES = ("step_kernel.cuh", "lattice.cuh", "march_kernel.cuh")
+
+
+def kernel_sha() -> str:
+    """Hash (16 hex digits) of the step kernels' sources."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2012_14729_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(workload: str, storage: str, stage: str):
     """DRAM bytes per node and step of the step kernel from the committed ncu
-    summary of this workload, valid only while the kernel source is unchanged."""
+    summary of this workload, valid only while the kernel sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2012_14729_gb300", "csrc", "step_kernel.cuh")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_sha()
         r = rec.get(f"{workload}/{storage}/{stage}")
         if r and r.get("kernel_sha") == sha:
             return float(r["dram_bytes_per_lup"])

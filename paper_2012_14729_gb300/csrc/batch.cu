@@ -83,10 +83,16 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
   constexpr int NT = BatchCfg<MODE>::NT;
   constexpr bool kAsync = sizeof(typename ST::T) == 4;
   extern __shared__ __align__(128) unsigned char sm[];
-  StepArgs* sa = reinterpret_cast<StepArgs*>(sm);  // this item's arguments
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kArgsBytes);
-  unsigned char* bx = sm + kArgsBytes + 128;
+  // the arguments of this item and of the next one (two buffers)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kArgsBytes);
+  unsigned char* bx = sm + 2 * kArgsBytes + 128;
   unsigned char* fs = bx + (MODE == kBoxes ? Boxes<ST>::BYTES : 0);
+  const auto copy_args = [&](int it, int buf) {
+    if (it >= nitems) return;
+    const int4* s = reinterpret_cast<const int4*>(&table[2 * items[it].x + bp]);
+    int4* d = reinterpret_cast<int4*>(sm + buf * kArgsBytes);
+    for (int w = threadIdx.x; w < (int)(sizeof(StepArgs) / 16); w += NT) d[w] = s[w];
+  };
 
   if constexpr (MODE == kBoxes) {
     if (threadIdx.x == 0) {
@@ -95,18 +101,16 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
     }
   }
   uint32_t parity = 0u;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  copy_args(blockIdx.x, 0);
+  int buf = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, buf ^= 1) {
     const int4 item = items[it];
     const StepArgs& ga = table[2 * item.x + bp];
-    // copy the instance's arguments to shared memory (16-byte words)
-    __syncthreads();  // the previous item is done with sa
-    {
-      const int4* s = reinterpret_cast<const int4*>(&ga);
-      int4* d = reinterpret_cast<int4*>(sa);
-      for (int w = threadIdx.x; w < (int)(sizeof(StepArgs) / 16); w += NT) d[w] = s[w];
-    }
+    // this item's arguments are in place, and every thread is done with the
+    // other buffer (the previous item's): fill it with the next item's
     __syncthreads();
-    const StepArgs& a = *sa;
+    copy_args(it + gridDim.x, buf ^ 1);
+    const StepArgs& a = *reinterpret_cast<const StepArgs*>(sm + buf * kArgsBytes);
     const int x0 = item.y, y0 = item.z;
     if constexpr (MODE == kBoxes) {
       if (tma_tile<ST>(a, x0, y0)) {
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
 
 template <int MODE>
 constexpr int batch_smem() {
-  return kArgsBytes + 128 + (MODE == kBoxes ? Boxes<StoreF32>::BYTES : 0) + kFieldsMax;
+  return 2 * kArgsBytes + 128 + (MODE == kBoxes ? Boxes<StoreF32>::BYTES : 0) + kFieldsMax;
 }
 
 template <int MODE, int TY>

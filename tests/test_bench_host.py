@@ -32,8 +32,7 @@ def test_workload_table_sizes():
 def test_traffic_records_follow_the_kernel_source():
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
         rec = json.load(fh)
-    src = os.path.join(ROOT, "paper_2012_14729_gb300", "csrc", "step_kernel.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = bench.kernel_sha()
     for key, r in rec.items():
         if key.startswith("_"):
             continue

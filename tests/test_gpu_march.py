@@ -1,6 +1,6 @@
 """GPU tests of the marching stage mode (persistent CTAs sweep column strips
-along y, a producer warp stages the pulled population rows into a ring of
-row slots): parity with the FP64 oracle at the plain-step bar, equality
+along y, staging the pulled population rows ahead into a shared-memory ring
+of row slots): parity with the FP64 oracle at the plain-step bar, equality
 with the gather mode to float32 rounding for every storage format, the
 16-bit bars, lattices whose CTA shares split at strip boundaries, graph
 replay, and the cases the mode refuses."""
