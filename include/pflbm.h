@@ -274,8 +274,8 @@ void pflbm_destroy(pflbm_domain* d);
 /* Device scratch of pflbm_adjoint_run: a checkpoint at the start of every
  * segment of ckpt_every steps but the last, the tape of one segment (24
  * float32 planes of nx * ny per step: pulled f, phi, grad phi, lap phi, mu,
- * force values, u, P, div(phi u), d_t(phi u)), two adjoint states and work
- * planes.  0 for invalid input: FP32 storage, periodic x, nsteps and
+ * force values, u, P, div(phi u), d_t(phi u)), a second such tape when there
+ * are two segments or more, two adjoint states and work planes.  0 for invalid input: FP32 storage, periodic x, nsteps and
  * ckpt_every >= 1, and 24 nx ny < 2^31 (the tape's 32-bit plane offsets;
  * about 89 M nodes). */
 size_t pflbm_adjoint_scratch_bytes(const pflbm_domain* d, int nsteps, int ckpt_every);
@@ -286,9 +286,12 @@ size_t pflbm_adjoint_scratch_bytes(const pflbm_domain* d, int nsteps, int ckpt_e
  * backwards through the steps.  Each segment but the last is recomputed from
  * its checkpoint by a taping step that records the step's intermediates; the
  * last is taped during the forward run (ckpt_every >= nsteps: no
- * recomputation at all).  Recomputation and reverse sweep of a segment are
- * replayed from CUDA graphs when the domain's stream can be captured (not on
- * the legacy default stream); the first call on a stream captures them.
+ * recomputation at all).  The recomputation of a segment runs on a stream the
+ * call creates (and destroys before returning) while the domain's stream
+ * reverses the segment after it, into the other of the two tapes.
+ * Recomputation and reverse sweep of a segment are replayed from CUDA graphs
+ * where the stream can be captured (the reverse sweep not on the legacy
+ * default stream); the first use in a call captures them.
  * Input dJ_dphiT: gradient of an objective J with respect to the final phi_T
  * (device [ny][nx]).  Outputs: dJ_dphi0 (device [ny][nx]) and, on the host,
  * dJ/dsigma and dJ/dM (FP64 accumulation; sigma through beta, kappa and the

@@ -788,7 +788,9 @@ void pflbm_destroy(pflbm_domain* d) {
 namespace {
 
 struct AdjLayout {
-  size_t ckpt, tape, work, adj[2], acc, final_state, total;
+  // tape[1]: a second tape, so that the recomputation of the segment before
+  // can run while a segment is reversed (two segments or more)
+  size_t ckpt, tape[2], work, adj[2], acc, final_state, total;
   size_t blob;       // bytes of one state blob
   size_t tape_step;  // bytes of one step's tape
   int ncp;
@@ -807,8 +809,14 @@ bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
   L->final_state = off;
   off += L->blob;
   L->tape_step = align_up((size_t)kTapePlanes * n * 4);
-  L->tape = off;  // one tape per step of a segment
-  off += (size_t)(every < nsteps ? every : nsteps) * L->tape_step;
+  const size_t seg_tape = (size_t)(every < nsteps ? every : nsteps) * L->tape_step;
+  L->tape[0] = off;  // one tape per step of a segment
+  off += seg_tape;
+  L->tape[1] = L->tape[0];
+  if (L->ncp > 1) {
+    L->tape[1] = off;
+    off += seg_tape;
+  }
   L->work = off;
   off = align_up(off + (size_t)kWorkPlanes * n * 4);
   for (int b = 0; b < 2; ++b) {
@@ -825,16 +833,40 @@ bool adj_layout(const pflbm_domain* d, int nsteps, int every, AdjLayout* L) {
 // segment, full length) and its reverse sweep keyed by (first segment, parity
 // of the adjoint buffers, full length).
 struct AdjGraphs {
-  cudaGraphExec_t rec[2][2] = {};
-  cudaGraphExec_t rev[2][2][2] = {};
+  cudaGraphExec_t rec[2][2][2] = {};     // [first][full][tape]
+  cudaGraphExec_t rev[2][2][2][2] = {};  // [first][parity][full][tape]
   ~AdjGraphs() {
     for (auto& a : rec)
-      for (auto& g : a)
-        if (g) cudaGraphExecDestroy(g);
-    for (auto& a : rev)
       for (auto& b : a)
         for (auto& g : b)
           if (g) cudaGraphExecDestroy(g);
+    for (auto& a : rev)
+      for (auto& b : a)
+        for (auto& c : b)
+          for (auto& g : c)
+            if (g) cudaGraphExecDestroy(g);
+  }
+};
+
+// Streams and events of the reverse sweep: the recomputation of segment c - 1
+// (checkpoint load and taping steps, on the auxiliary stream) runs while
+// segment c is reversed on the domain's stream.
+struct AdjOverlap {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fwd = nullptr, rec = nullptr, rev[2] = {nullptr, nullptr};
+  cudaError_t create() {
+    cudaError_t e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fwd, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&rec, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&rev[k], cudaEventDisableTiming);
+    return e;
+  }
+  ~AdjOverlap() {
+    if (aux) cudaStreamSynchronize(aux);
+    for (cudaEvent_t ev : {fwd, rec, rev[0], rev[1]})
+      if (ev) cudaEventDestroy(ev);
+    if (aux) cudaStreamDestroy(aux);
   }
 };
 
@@ -908,7 +940,7 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
     for (int j = 0; j < seg; ++j) {
       StepArgs a = make_args(d, d->cur);
       a.first = d->t == 0;
-      a.tape = reinterpret_cast<float*>(S + L.tape + (size_t)j * L.tape_step);
+      a.tape = reinterpret_cast<float*>(S + L.tape[0] + (size_t)j * L.tape_step);
       if ((e = launch_tape_step(d->par.force, a, d->stream)) != cudaSuccess)
         return fail("adjoint forward");
       d->cur = 1 - d->cur;
@@ -937,31 +969,51 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
   A.W = reinterpret_cast<float*>(S + L.work);
   A.acc = acc;
   AdjGraphs graphs;
-  for (int c = L.ncp - 1; c >= 0; --c) {
-    const int seg = c + 1 < L.ncp ? ckpt_every : nsteps - c * ckpt_every;
-    const int first = c == 0, full = seg == ckpt_every;
-    // recompute the segment from its checkpoint (loaded into buffer 0),
-    // taping every step (the last segment was taped by the forward run)
-    if (c + 1 < L.ncp) {
-      if ((st = pflbm_load_state(d, S + L.ckpt + (size_t)c * L.blob, 1)) != PFLBM_OK) return st;
-      e = run_captured(d->stream, &graphs.rec[first][full], [&]() -> cudaError_t {
-        for (int j = 0; j < seg; ++j) {
+  AdjOverlap ov;
+  if (L.ncp > 1) {
+    if ((e = ov.create()) != cudaSuccess) return fail("adjoint streams");
+    if ((e = cudaEventRecord(ov.fwd, d->stream)) != cudaSuccess) return fail("adjoint streams");
+  }
+  // segment c reads the tape its recomputation wrote: the last segment the
+  // one the forward run taped, then the two tapes alternate
+  const auto tape_index = [&](int c) { return (L.ncp - 1 - c) & 1; };
+  // Recompute segment c (never the last) from its checkpoint on the auxiliary
+  // stream, taping every step, and mark its end with ov.rec.
+  const auto recompute = [&](int c) -> pflbm_status {
+    const int first = c == 0, tb = tape_index(c);
+    cudaStream_t keep = d->stream;
+    d->stream = ov.aux;  // the checkpoint load runs on the auxiliary stream too
+    pflbm_status st2 = pflbm_load_state(d, S + L.ckpt + (size_t)c * L.blob, 1);
+    if (st2 == PFLBM_OK) {
+      e = run_captured(ov.aux, &graphs.rec[first][1][tb], [&]() -> cudaError_t {
+        for (int j = 0; j < ckpt_every; ++j) {
           StepArgs a = make_args(d, j & 1);
           a.first = first && j == 0;
-          a.tape = reinterpret_cast<float*>(S + L.tape + (size_t)j * L.tape_step);
-          const cudaError_t el = launch_tape_step(d->par.force, a, d->stream);
+          a.tape = reinterpret_cast<float*>(S + L.tape[tb] + (size_t)j * L.tape_step);
+          const cudaError_t el = launch_tape_step(d->par.force, a, ov.aux);
           if (el != cudaSuccess) return el;
         }
         return cudaSuccess;
       });
-      if (e != cudaSuccess) return fail("adjoint recompute");
+      if (e == cudaSuccess) e = cudaEventRecord(ov.rec, ov.aux);
+      if (e != cudaSuccess) st2 = fail("adjoint recompute");
     }
+    d->stream = keep;
+    return st2;
+  };
+  for (int c = L.ncp - 1; c >= 0; --c) {
+    const int seg = c + 1 < L.ncp ? ckpt_every : nsteps - c * ckpt_every;
+    const int first = c == 0, full = seg == ckpt_every, tb = tape_index(c);
+    // the recomputation of this segment (the last one was taped by the forward
+    // run) has finished before its reverse starts
+    if (c + 1 < L.ncp && (e = cudaStreamWaitEvent(d->stream, ov.rec, 0)) != cudaSuccess)
+      return fail("adjoint streams");
     // reverse through the segment
     const int cur0 = cur;
-    e = run_captured(d->stream, &graphs.rev[first][cur0][full], [&]() -> cudaError_t {
+    e = run_captured(d->stream, &graphs.rev[first][cur0][full][tb], [&]() -> cudaError_t {
       int cc = cur0;
       for (int j = seg - 1; j >= 0; --j) {
-        A.tape = reinterpret_cast<const float*>(S + L.tape + (size_t)j * L.tape_step);
+        A.tape = reinterpret_cast<const float*>(S + L.tape[tb] + (size_t)j * L.tape_step);
         A.first = first && j == 0;
         A.ain = adj[cc];
         A.aout = adj[1 - cc];
@@ -973,6 +1025,16 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
     });
     if (e != cudaSuccess) return fail("adjoint step");
     cur = (seg & 1) ? 1 - cur0 : cur0;
+    if (L.ncp > 1 && (e = cudaEventRecord(ov.rev[c & 1], d->stream)) != cudaSuccess)
+      return fail("adjoint streams");
+    // meanwhile the segment before is recomputed into the tape that the
+    // segment after this one was reversed from (or, first, the unused one)
+    if (c >= 1) {
+      const cudaEvent_t free_tape = c + 1 < L.ncp ? ov.rev[(c + 1) & 1] : ov.fwd;
+      if ((e = cudaStreamWaitEvent(ov.aux, free_tape, 0)) != cudaSuccess)
+        return fail("adjoint streams");
+      if ((st = recompute(c - 1)) != PFLBM_OK) return st;
+    }
   }
   // through the initial state to phi0
   A.ain = adj[cur];
