@@ -118,6 +118,12 @@ __device__ __forceinline__ void acc_add(double* acc, double v0, double v1, doubl
 #define TP(pl) (A.tape + (size_t)(pl) * n)
 #define AI(pl) (A.ain + (size_t)(kAdjScalar + (pl)) * n)
 #define AO(pl) (A.aout + (size_t)(kAdjScalar + (pl)) * n)
+// element m of a plane, the offset formed in 32 bits (the host refuses grids
+// whose planes would reach 2^31 elements)
+#define TPK(pl, m) (A.tape[(unsigned)((pl) * n + (m))])
+#define AIK(pl, m) (A.ain[(unsigned)((kAdjScalar + (pl)) * n + (m))])
+#define AOK(pl, m) (A.aout[(unsigned)((kAdjScalar + (pl)) * n + (m))])
+#define WKK(pl, m) (A.W[(unsigned)((pl) * n + (m))])
 #define SI(m) (reinterpret_cast<const float4*>(A.ain)[m])
 #define SO(m) (reinterpret_cast<float4*>(A.aout)[m])
 #define WK(pl) (A.W + (size_t)(pl) * n)
@@ -125,10 +131,10 @@ __device__ __forceinline__ void acc_add(double* acc, double v0, double v1, doubl
 // Full adjoint of pre-collision population i at node m of step t + 1.
 // (s: the node's scalar block SB, JX, JY, PHI, read as one 16-byte load)
 __device__ __forceinline__ float fb_full(const AdjArgs& A, int n, int i, int m, float4 s) {
-  return AI(AP_F0 + i)[m] + s.x + qcx(i) * s.y + qcy(i) * s.z;
+  return AIK(AP_F0 + i, m) + s.x + qcx(i) * s.y + qcy(i) * s.z;
 }
 __device__ __forceinline__ float hb_full(const AdjArgs& A, int n, int i, int m, float4 s) {
-  return AI(AP_H0 + i)[m] + s.w;
+  return AIK(AP_H0 + i, m) + s.w;
 }
 
 // streaming transpose + collision transpose (+ bounce-back terms); built for
@@ -140,14 +146,14 @@ __global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
   const Geo& g = A.g;
   double deta = 0.0;
   if (live) {
-    const float phi = TP(TP_PHI)[k], ux = TP(TP_UX)[k], uy = TP(TP_UY)[k];
-    const float Fx = TP(TP_FX)[k], Fy = TP(TP_FY)[k], Pr = TP(TP_PR)[k], mu = TP(TP_MU)[k];
+    const float phi = TPK(TP_PHI, k), ux = TPK(TP_UX, k), uy = TPK(TP_UY, k);
+    const float Fx = TPK(TP_FX, k), Fy = TPK(TP_FY, k), Pr = TPK(TP_PR, k), mu = TPK(TP_MU, k);
     constexpr float c3 = 1.0f / 3.0f;
     const float rho = P.rho_mid + P.drho_half * phi;
     const float irho = 1.0f / rho, rho3 = rho * c3;
     const float mv = P.mu_mid + P.mu_dhalf * phi;
     const float om = 1.0f / (0.5f + 3.0f * mv * irho);
-    const float Rx3 = P.drho_half * TP(TP_GX)[k] * c3, Ry3 = P.drho_half * TP(TP_GY)[k] * c3;
+    const float Rx3 = P.drho_half * TPK(TP_GX, k) * c3, Ry3 = P.drho_half * TPK(TP_GY, k) * c3;
     const float uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy, uR = ux * Rx3 + uy * Ry3;
     const float om1 = 1.0f - om, cff = 1.0f - 0.5f * om, omh1 = 1.0f - P.inv_tau_h;
     float phib = 0.0f, rhob = 0.0f, uxb = 0.0f, uyb = 0.0f, Pb = 0.0f, Fxb = 0.0f, Fyb = 0.0f;
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
       const float cF = qcx(i) * Fx + qcy(i) * Fy;
       const float cR = qcx(i) * Rx3 + qcy(i) * Ry3;
       const float Fi = qw(i) * ((1.0f + s) * (cF - uF) + s * (cR - uR));
-      AO(AP_F0 + i)[k] = om1 * fpb;
-      omb += fpb * (-TP(TP_F0 + i)[k] + feq - 0.5f * Fi);
+      AOK(AP_F0 + i, k) = om1 * fpb;
+      omb += fpb * (-TPK(TP_F0 + i, k) + feq - 0.5f * Fi);
       const float feqb = om * fpb, Fib = cff * fpb;
       Pb += qw(i) * feqb;
       rhob += (qw(i) * c3) * s * feqb;
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
       uxb += sb * ((3.0f + 9.0f * cu) * qcx(i) - 3.0f * ux);
       uyb += sb * ((3.0f + 9.0f * cu) * qcy(i) - 3.0f * uy);
       // h
-      AO(AP_H0 + i)[k] = omh1 * hpb;
+      AOK(AP_H0 + i, k) = omh1 * hpb;
       const float heqb = hpb * P.inv_tau_h, Hb = P.hforce * hpb;
       if (i == 0) {
         phib += heqb;
@@ -222,19 +228,19 @@ __global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
     Rxb *= c3;
     Ryb *= c3;
     deta = (double)etab;
-    WK(B_PHI)[k] = phib;
-    WK(B_RHO)[k] = rhob;
-    WK(B_UX)[k] = uxb;
-    WK(B_UY)[k] = uyb;
-    WK(B_P)[k] = Pb;
-    WK(B_FX)[k] = Fxb;
-    WK(B_FY)[k] = Fyb;
-    WK(B_GX)[k] = P.drho_half * Rxb;  // R = (rho1 - rho2)/2 grad phi
-    WK(B_GY)[k] = P.drho_half * Ryb;
-    WK(B_MU)[k] = mub;
-    WK(B_DIV)[k] = divb;
-    WK(B_DTX)[k] = dtxb;
-    WK(B_DTY)[k] = dtyb;
+    WKK(B_PHI, k) = phib;
+    WKK(B_RHO, k) = rhob;
+    WKK(B_UX, k) = uxb;
+    WKK(B_UY, k) = uyb;
+    WKK(B_P, k) = Pb;
+    WKK(B_FX, k) = Fxb;
+    WKK(B_FY, k) = Fyb;
+    WKK(B_GX, k) = P.drho_half * Rxb;  // R = (rho1 - rho2)/2 grad phi
+    WKK(B_GY, k) = P.drho_half * Ryb;
+    WKK(B_MU, k) = mub;
+    WKK(B_DIV, k) = divb;
+    WKK(B_DTX, k) = dtxb;
+    WKK(B_DTY, k) = dtyb;
   }
   acc_add(A.acc, 0.0, 0.0, deta, 0.0);
 }
@@ -259,7 +265,7 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
   float pxb = stencil_T<false>(divb, g, x, y, 0, -1.0f);
   float pyb = stencil_T<false>(divb, g, x, y, 1, -1.0f);
   Tail o;
-  o.phib = WK(B_PHI)[k];
+  o.phib = WKK(B_PHI, k);
   if (g.wall && (y == 0 || y == g.ny - 1)) {
     // ghost adjoint of p_x at (x, -1) or (x, ny): nodes of this row whose
     // stencil reads it; its 2 u_w phi(x, row) part goes to phi
@@ -270,39 +276,39 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
       if (qcy(i) == cyw) ga += 3.0f * qw(i) * qcx(i) * divb[y * g.nx + wx(g, x - qcx(i))];
     o.phib += 2.0f * (y == 0 ? P.uwb : P.uwt) * ga;
   }
-  pxb += AI(AP_QX)[k];
-  pyb += AI(AP_QY)[k];
-  const float dtxb = A.first ? 0.0f : WK(B_DTX)[k], dtyb = A.first ? 0.0f : WK(B_DTY)[k];
+  pxb += AIK(AP_QX, k);
+  pyb += AIK(AP_QY, k);
+  const float dtxb = A.first ? 0.0f : WKK(B_DTX, k), dtyb = A.first ? 0.0f : WKK(B_DTY, k);
   pxb += dtxb;
   pyb += dtyb;
   // macroscopic relations
-  const float phi = TP(TP_PHI)[k], ux = TP(TP_UX)[k], uy = TP(TP_UY)[k];
-  const float gx = TP(TP_GX)[k], gy = TP(TP_GY)[k];
+  const float phi = TPK(TP_PHI, k), ux = TPK(TP_UX, k), uy = TPK(TP_UY, k);
+  const float gx = TPK(TP_GX, k), gy = TPK(TP_GY, k);
   constexpr float c6 = 1.0f / 6.0f;
   const float rho = P.rho_mid + P.drho_half * phi;
   const float irho = 1.0f / rho;
   const float Rx = P.drho_half * gx, Ry = P.drho_half * gy;
-  const float Pb = WK(B_P)[k];
+  const float Pb = WKK(B_P, k);
   o.phib += pxb * ux + pyb * uy;
-  const float uxb = WK(B_UX)[k] + phi * pxb + Rx * c6 * Pb;
-  const float uyb = WK(B_UY)[k] + phi * pyb + Ry * c6 * Pb;
-  o.Gxb = WK(B_GX)[k] + P.drho_half * (ux * c6 * Pb);
-  o.Gyb = WK(B_GY)[k] + P.drho_half * (uy * c6 * Pb);
+  const float uxb = WKK(B_UX, k) + phi * pxb + Rx * c6 * Pb;
+  const float uyb = WKK(B_UY, k) + phi * pyb + Ry * c6 * Pb;
+  o.Gxb = WKK(B_GX, k) + P.drho_half * (ux * c6 * Pb);
+  o.Gyb = WKK(B_GY, k) + P.drho_half * (uy * c6 * Pb);
   if (own) {
-    AO(AP_QX)[k] = -dtxb;
-    AO(AP_QY)[k] = -dtyb;
+    AOK(AP_QX, k) = -dtxb;
+    AOK(AP_QY, k) = -dtyb;
     // (PHI, the w component, is written by the finishing stage)
     SO(k) = make_float4(Pb, 3.0f * uxb * irho, 3.0f * uyb * irho, 0.0f);
   }
-  const float Fxb = WK(B_FX)[k] + 0.5f * uxb * irho;  // adjoint of F_sf
-  const float Fyb = WK(B_FY)[k] + 0.5f * uyb * irho;
-  float rhob = WK(B_RHO)[k] - (ux * uxb + uy * uyb) * irho;
+  const float Fxb = WKK(B_FX, k) + 0.5f * uxb * irho;  // adjoint of F_sf
+  const float Fyb = WKK(B_FY, k) + 0.5f * uyb * irho;
+  float rhob = WKK(B_RHO, k) - (ux * uxb + uy * uyb) * irho;
   rhob += P.gx * Fxb + P.gy * Fyb;
   o.phib += P.drho_half * rhob;
   // pointwise part of the force
-  o.mub = WK(B_MU)[k];
+  o.mub = WKK(B_MU, k);
   o.Lb = o.w0 = o.w1 = o.w2 = 0.0f;
-  const float a0 = TP(TP_A0)[k], a1 = TP(TP_A1)[k];
+  const float a0 = TPK(TP_A0, k), a1 = TPK(TP_A1, k);
   switch (A.form) {
     case kSTF1:
     case kSTF2:  // F_sf = kappa (a0, a1) / kappa: the tape holds F_sf
@@ -316,14 +322,14 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
       o.w1 = -phi * Fyb;
       break;
     case kCPF2: {
-      const float mu = TP(TP_MU)[k];
+      const float mu = TPK(TP_MU, k);
       o.mub += gx * Fxb + gy * Fyb;
       o.Gxb += mu * Fxb;
       o.Gyb += mu * Fyb;
       break;
     }
     case kPF1: {
-      const float L = TP(TP_L)[k];
+      const float L = TPK(TP_L, k);
       o.Gxb += -P.kappa * L * Fxb;
       o.Gyb += -P.kappa * L * Fyb;
       o.Lb = -P.kappa * (gx * Fxb + gy * Fyb);
@@ -369,7 +375,7 @@ template <class ST>
 __device__ __forceinline__ void late_node(const AdjArgs& A, int n, int k, Tail& v, const ST& st,
                                           double& db, double& dk) {
   const Phys& P = A.p;
-  const float gx = TP(TP_GX)[k], gy = TP(TP_GY)[k], phi = TP(TP_PHI)[k];
+  const float gx = TPK(TP_GX, k), gy = TPK(TP_GY, k), phi = TPK(TP_PHI, k);
   switch (A.form) {
     case kSTF1:
     case kSTF2: {
@@ -407,7 +413,7 @@ __device__ __forceinline__ void late_node(const AdjArgs& A, int n, int k, Tail& 
   v.phib += P.beta4 * (3.0f * phi * phi - 1.0f) * v.mub;
   v.Lb += -P.kappa * v.mub;
   db += (double)(phi * (phi * phi - 1.0f) * v.mub);
-  dk += (double)(-TP(TP_L)[k] * v.mub);
+  dk += (double)(-TPK(TP_L, k) * v.mub);
 }
 
 // Transposed stencils on a shared-memory tile of row stride S: node at local
@@ -545,14 +551,14 @@ __global__ void __launch_bounds__(kAB) k_adj_mid(const AdjArgs A) {
   double dk = 0.0, ds = 0.0;
   if (live) {
     const Tail t = mid_node(A, n, x, y, k, true, dk, ds);
-    WK(B_PHI)[k] = t.phib;
-    WK(B_GX)[k] = t.Gxb;
-    WK(B_GY)[k] = t.Gyb;
-    WK(B_MU)[k] = t.mub;
-    WK(B_L)[k] = t.Lb;
-    WK(B_W0)[k] = t.w0;
-    WK(B_W1)[k] = t.w1;
-    WK(B_W2)[k] = t.w2;
+    WKK(B_PHI, k) = t.phib;
+    WKK(B_GX, k) = t.Gxb;
+    WKK(B_GY, k) = t.Gyb;
+    WKK(B_MU, k) = t.mub;
+    WKK(B_L, k) = t.Lb;
+    WKK(B_W0, k) = t.w0;
+    WKK(B_W1, k) = t.w1;
+    WKK(B_W2, k) = t.w2;
   }
   acc_add(A.acc, 0.0, dk, 0.0, ds);
 }
@@ -563,20 +569,20 @@ __global__ void __launch_bounds__(kAB) k_adj_late(const AdjArgs A) {
   if (live) {
     const Geo& g = A.g;
     Tail v;
-    v.phib = WK(B_PHI)[k];
-    v.Gxb = WK(B_GX)[k];
-    v.Gyb = WK(B_GY)[k];
-    v.mub = WK(B_MU)[k];
-    v.Lb = WK(B_L)[k];
+    v.phib = WKK(B_PHI, k);
+    v.Gxb = WKK(B_GX, k);
+    v.Gyb = WKK(B_GY, k);
+    v.mub = WKK(B_MU, k);
+    v.Lb = WKK(B_L, k);
     const float* w[3] = {WK(B_W0), WK(B_W1), WK(B_W2)};
     const auto st = [&](int f, int axis, float parity) {
       return stencil_T<false>(w[f], g, x, y, axis, parity);
     };
     late_node(A, n, k, v, st, db, dk);
-    WK(B_PHI)[k] = v.phib;
-    WK(B_GX)[k] = v.Gxb;
-    WK(B_GY)[k] = v.Gyb;
-    WK(B_L)[k] = v.Lb;
+    WKK(B_PHI, k) = v.phib;
+    WKK(B_GX, k) = v.Gxb;
+    WKK(B_GY, k) = v.Gyb;
+    WKK(B_L, k) = v.Lb;
   }
   acc_add(A.acc, db, dk, 0.0, 0.0);
 }
@@ -587,7 +593,7 @@ __global__ void __launch_bounds__(kAB) k_adj_finish(const AdjArgs A) {
   if (!live) return;
   const Geo& g = A.g;
   reinterpret_cast<float*>(A.aout)[4 * k + 3] =  // the PHI (w) component of SO(k)
-      WK(B_PHI)[k] + stencil_T<false>(WK(B_GX), g, x, y, 0, 1.0f) +
+      WKK(B_PHI, k) + stencil_T<false>(WK(B_GX), g, x, y, 0, 1.0f) +
       stencil_T<false>(WK(B_GY), g, x, y, 1, 1.0f) + stencil_T<true>(WK(B_L), g, x, y, 0, 1.0f);
 }
 
@@ -633,8 +639,8 @@ __global__ void __launch_bounds__(kAB) k_adj_init_pt(const AdjArgs A, const floa
     de = (double)(mu * hsum);
     db = (double)(phi * (phi * phi - 1.0f) * mub);
     dk = (double)(-L * mub);
-    WK(B_PHI)[k] = hb0 + P.beta4 * (3.0f * phi * phi - 1.0f) * mub;
-    WK(B_L)[k] = -P.kappa * mub;
+    WKK(B_PHI, k) = hb0 + P.beta4 * (3.0f * phi * phi - 1.0f) * mub;
+    WKK(B_L, k) = -P.kappa * mub;
   }
   acc_add(A.acc, db, dk, de, 0.0);
 }
@@ -642,7 +648,7 @@ __global__ void __launch_bounds__(kAB) k_adj_init_pt(const AdjArgs A, const floa
 __global__ void __launch_bounds__(kAB) k_adj_init_out(const AdjArgs A, float* dphi0) {
   ADJ_NODE
   if (!live) return;
-  dphi0[k] = WK(B_PHI)[k] + stencil_T<true>(WK(B_L), A.g, x, y, 0, 1.0f);
+  dphi0[k] = WKK(B_PHI, k) + stencil_T<true>(WK(B_L), A.g, x, y, 0, 1.0f);
 }
 
 cudaError_t launch_adjoint_init(const AdjArgs& A, const float* phi0, float* dphi0,

@@ -122,35 +122,34 @@ __device__ __forceinline__ void store_h(const StepArgs& a, int idx, float v) {
 }
 
 // The same in the storage scale of the format (the step kernel's arithmetic).
+// The element offset of plane pl, index idx is formed in 32 bits (the host
+// refuses lattices whose 9 planes reach 2^31 elements), so that one 32-bit
+// add and one widening multiply-add address each population.
 template <class ST, int I>
 __device__ __forceinline__ float load_fs(const StepArgs& a, int idx) {
   using T = typename ST::T;
-  const T* base = reinterpret_cast<const T*>(a.f_in) + (size_t)I * a.L.plane;
-  return ST::raw(__ldg(base + idx));
+  return ST::raw(__ldg(reinterpret_cast<const T*>(a.f_in) + (unsigned)(I * a.L.plane + idx)));
 }
 template <class ST, int I>
 __device__ __forceinline__ float load_hs(const StepArgs& a, int idx) {
   using T = typename ST::T;
-  if constexpr (ST::kSplitH0 && I == 0) return __ldg(a.h0_in + idx);
+  if constexpr (ST::kSplitH0 && I == 0) return __ldg(a.h0_in + (unsigned)idx);
   const int pl = ST::kSplitH0 ? I - 1 : I;
-  const T* base = reinterpret_cast<const T*>(a.h_in) + (size_t)pl * a.L.plane;
-  return ST::raw(__ldg(base + idx));
+  return ST::raw(__ldg(reinterpret_cast<const T*>(a.h_in) + (unsigned)(pl * a.L.plane + idx)));
 }
 template <class ST, int I>
 __device__ __forceinline__ void store_fs(const StepArgs& a, int idx, float v) {
   using T = typename ST::T;
-  T* base = reinterpret_cast<T*>(a.f_out) + (size_t)I * a.L.plane;
-  base[idx] = ST::enc_raw(v);
+  reinterpret_cast<T*>(a.f_out)[(unsigned)(I * a.L.plane + idx)] = ST::enc_raw(v);
 }
 template <class ST, int I>
 __device__ __forceinline__ void store_hs(const StepArgs& a, int idx, float v) {
   using T = typename ST::T;
   if constexpr (ST::kSplitH0 && I == 0) {
-    a.h0_out[idx] = v;
+    a.h0_out[(unsigned)idx] = v;
   } else {
     const int pl = ST::kSplitH0 ? I - 1 : I;
-    T* base = reinterpret_cast<T*>(a.h_out) + (size_t)pl * a.L.plane;
-    base[idx] = ST::enc_raw(v);
+    reinterpret_cast<T*>(a.h_out)[(unsigned)(pl * a.L.plane + idx)] = ST::enc_raw(v);
   }
 }
 
