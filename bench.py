@@ -126,7 +126,8 @@ def measured_peaks():
 
 
 # the step kernel each stage mode launches (the dominant kernel of a step)
-KERNEL_OF_STAGE = {"boxes": "k_step_boxes", "gather": "k_step_gather", "march": "k_step_march"}
+KERNEL_OF_STAGE = {"boxes": "k_step_boxes", "gather": "k_step_gather", "march": "k_step_march",
+                   "gather8": "k_step_gather"}
 
 
 # the sources the step kernels are compiled from
@@ -561,7 +562,7 @@ def main():
     ap.add_argument("--workload", default="bubble_512x1024")
     ap.add_argument("--form", default="STF1")
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp16", "bf16"))
-    ap.add_argument("--stage", default="auto", choices=("auto", "boxes", "gather", "march"))
+    ap.add_argument("--stage", default="auto", choices=("auto", "boxes", "gather", "march", "gather8"))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--load-seconds", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

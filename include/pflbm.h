@@ -202,7 +202,14 @@ pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
  *   PFLBM_STAGE_BOXES   TMA box loads of each tile's population planes into
  *                       shared memory, persistent CTAs (2 per SM)
  *   PFLBM_STAGE_GATHER  L1-cached gathers straight from the planes, one CTA
- *                       per tile (the default)
+ *                       of 256 threads per tile, two collision nodes per
+ *                       thread (the default)
+ *   PFLBM_STAGE_GATHER8 the same gathers on 32 x 8 tiles, one CTA of 256
+ *                       threads per tile and one collision node per thread:
+ *                       each thread pulls its own node first and keeps its
+ *                       populations in registers for the collision, which
+ *                       then re-reads no plane (finer-grained waves on
+ *                       lattices of a few hundred tiles)
  *   PFLBM_STAGE_MARCH   persistent CTAs sweep column strips along y; the
  *                       pulled population rows are copied two iterations
  *                       ahead into a ring in shared memory (cp.async), the
@@ -212,7 +219,12 @@ pflbm_status pflbm_set_graphs(pflbm_domain* d, int enable);
  *                       or 8 (16-bit storage), ny >= 8, no side walls;
  *                       EINVAL otherwise.  The batch refuses it.
  * All compute the same step; results agree to float32 rounding order. */
-enum { PFLBM_STAGE_BOXES = 0, PFLBM_STAGE_GATHER = 1, PFLBM_STAGE_MARCH = 2 };
+enum {
+  PFLBM_STAGE_BOXES = 0,
+  PFLBM_STAGE_GATHER = 1,
+  PFLBM_STAGE_MARCH = 2,
+  PFLBM_STAGE_GATHER8 = 3
+};
 pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode);
 int pflbm_get_stage_mode(const pflbm_domain* d);
 

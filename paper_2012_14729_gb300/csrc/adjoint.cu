@@ -140,7 +140,7 @@ __device__ __forceinline__ float hb_full(const AdjArgs& A, int n, int i, int m, 
 // streaming transpose + collision transpose (+ bounce-back terms); built for
 // 8 blocks per SM (64 registers): the kernel is bound by the latency of its
 // gathers, so more resident warps beat the few spilled registers
-__global__ void __launch_bounds__(kAB, 8) k_adj_collide(const AdjArgs A) {
+__global__ void __launch_bounds__(kAB, 7) k_adj_collide(const AdjArgs A) {
   ADJ_NODE
   const Phys& P = A.p;
   const Geo& g = A.g;

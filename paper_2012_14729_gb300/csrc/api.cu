@@ -447,7 +447,7 @@ pflbm_status pflbm_init_phi(pflbm_domain* d, const float* phi0, int on_device) {
 
 pflbm_status pflbm_set_stage_mode(pflbm_domain* d, int mode) {
   if (!d || mode < 0 || mode >= kNumModes) return PFLBM_EINVAL;
-  if (d->wall_x && mode != kGather) {
+  if (d->wall_x && mode != kGather && mode != kGather8) {
     set_msg("pflbm_set_stage_mode: side walls are staged by gathers only");
     return PFLBM_EINVAL;
   }
@@ -481,7 +481,7 @@ pflbm_status pflbm_autotune(pflbm_domain* d, int trial_steps, int* mode_out) {
   float best = 1e30f;
   int best_mode = d->mode;
   for (int m = 0; m < kNumModes && e == cudaSuccess; ++m) {
-    if (d->wall_x && m != kGather) continue;  // side walls: gathers only
+    if (d->wall_x && m != kGather && m != kGather8) continue;  // side walls: gathers only
     if (m == kMarch && !march_ok(d)) continue;
     e = launch_step_mode(d, m, a);  // warm-up (also sets kernel attributes)
     if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);

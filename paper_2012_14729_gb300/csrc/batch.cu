@@ -26,14 +26,14 @@ __device__ __forceinline__ void gather_item(const StepArgs& a, int form, unsigne
   using S = GatherSrc<ST, INNER>;
   const S src{};
   switch (form) {
-    case kSTF1: step_tile<kSTF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    case kSTF2: step_tile<kSTF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    case kCPF1: step_tile<kCPF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    case kCPF2: step_tile<kCPF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    case kPF1: step_tile<kPF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    case kPF2: step_tile<kPF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    case kCSF1: step_tile<kCSF1, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
-    default: step_tile<kCSF2, ST, NT, S, false, TY>(a, src, fs, x0, y0); break;
+    case kSTF1: step_tile<kSTF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kSTF2: step_tile<kSTF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kCPF1: step_tile<kCPF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kCPF2: step_tile<kCPF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kPF1: step_tile<kPF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kPF2: step_tile<kPF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kCSF1: step_tile<kCSF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    default: step_tile<kCSF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
   }
 }
 
@@ -44,14 +44,14 @@ __device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, 
     static_assert(TY == kTY, "box staging is laid out for full tiles");
     const BoxSrc<ST> src{bx};
     switch (form) {
-      case kSTF1: step_tile<kSTF1, ST, NT>(a, src, fs, x0, y0); break;
-      case kSTF2: step_tile<kSTF2, ST, NT>(a, src, fs, x0, y0); break;
-      case kCPF1: step_tile<kCPF1, ST, NT>(a, src, fs, x0, y0); break;
-      case kCPF2: step_tile<kCPF2, ST, NT>(a, src, fs, x0, y0); break;
-      case kPF1: step_tile<kPF1, ST, NT>(a, src, fs, x0, y0); break;
-      case kPF2: step_tile<kPF2, ST, NT>(a, src, fs, x0, y0); break;
-      case kCSF1: step_tile<kCSF1, ST, NT>(a, src, fs, x0, y0); break;
-      default: step_tile<kCSF2, ST, NT>(a, src, fs, x0, y0); break;
+      case kSTF1: step_tile<kSTF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kSTF2: step_tile<kSTF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kCPF1: step_tile<kCPF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kCPF2: step_tile<kCPF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kPF1: step_tile<kPF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kPF2: step_tile<kPF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kCSF1: step_tile<kCSF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      default: step_tile<kCSF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
     }
   } else if (inner_tile<TY>(a.L, x0, y0)) {
     gather_item<ST, NT, true, TY>(a, form, fs, x0, y0);
@@ -85,13 +85,24 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
   extern __shared__ __align__(128) unsigned char sm[];
   // the arguments of this item and of the next one (two buffers)
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kArgsBytes);
+  // the descriptors of this item and of the next one (two slots)
+  int4* desc = reinterpret_cast<int4*>(sm + 2 * kArgsBytes + 16);
   unsigned char* bx = sm + 2 * kArgsBytes + 128;
   unsigned char* fs = bx + (MODE == kBoxes ? Boxes<ST>::BYTES : 0);
+  // Copy the arguments of item it into buffer buf by cp.async (completed by
+  // the wait before the next CTA barrier).  Gathers read no tensor map, so
+  // their copy starts past the three maps.
+  constexpr int kFrom = MODE == kBoxes ? 0 : (int)(offsetof(StepArgs, use_tma) / 16);
+  static_assert(sizeof(StepArgs) % 16 == 0, "whole 16-byte chunks");
   const auto copy_args = [&](int it, int buf) {
-    if (it >= nitems) return;
-    const int4* s = reinterpret_cast<const int4*>(&table[2 * items[it].x + bp]);
-    int4* d = reinterpret_cast<int4*>(sm + buf * kArgsBytes);
-    for (int w = threadIdx.x; w < (int)(sizeof(StepArgs) / 16); w += NT) d[w] = s[w];
+    if (it < nitems) {
+      const int4* s = reinterpret_cast<const int4*>(&table[2 * items[it].x + bp]);
+      int4* d = reinterpret_cast<int4*>(sm + buf * kArgsBytes);
+      for (int w = kFrom + threadIdx.x; w < (int)(sizeof(StepArgs) / 16); w += NT)
+        cp_async16(d + w, s + w, true);
+      if (threadIdx.x == NT - 1) cp_async16(desc + buf, items + it, true);
+    }
+    cp_async_commit();
   };
 
   if constexpr (MODE == kBoxes) {
@@ -104,11 +115,13 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
   copy_args(blockIdx.x, 0);
   int buf = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x, buf ^= 1) {
-    const int4 item = items[it];
-    const StepArgs& ga = table[2 * item.x + bp];
-    // this item's arguments are in place, and every thread is done with the
-    // other buffer (the previous item's): fill it with the next item's
+    // this item's arguments and descriptor are in place, and every thread
+    // is done with the other buffer and slot (the previous item's): fill
+    // them with the next item's
+    cp_async_wait_all();
     __syncthreads();
+    const int4 item = desc[buf];
+    const StepArgs& ga = table[2 * item.x + bp];
     copy_args(it + gridDim.x, buf ^ 1);
     const StepArgs& a = *reinterpret_cast<const StepArgs*>(sm + buf * kArgsBytes);
     const int x0 = item.y, y0 = item.z;

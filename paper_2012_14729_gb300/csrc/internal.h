@@ -92,7 +92,10 @@ constexpr int kShortRows = 8;
 //            population rows staged ahead into a shared-memory ring by
 //            cp.async (march_kernel.cuh); single domains only, periodic x
 //            with nx a multiple of the 16-byte chunk, no side walls
-enum StageMode { kBoxes = 0, kGather = 1, kMarch = 2, kNumModes = 3 };
+//   kGather8 the gathers on tiles of kShortRows rows, one collision node per
+//            thread of a 256-thread CTA, whose own node's populations stay in
+//            registers from the pull to the collision; four CTAs per SM
+enum StageMode { kBoxes = 0, kGather = 1, kMarch = 2, kGather8 = 3, kNumModes = 4 };
 constexpr int kNumBatchModes = 2;  // the batch stages by boxes or gathers
 constexpr int kThreadsBoxes = 512;
 constexpr int kThreadsGather = 256;

@@ -43,16 +43,6 @@ constexpr int kMRing = 8;                  // rows of the field rings (power of 
 constexpr int kMThreads = 256;             // threads per CTA (8 warps)
 constexpr int kMBlocks = 2;                // CTAs per SM
 
-// 16-byte asynchronous copy global -> shared, bypassing L1; zero-filled when
-// !valid (nothing is read then)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
-               "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
 // wait until at most one committed group of this thread is still in flight
 __device__ __forceinline__ void cp_async_wait_one() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");

@@ -90,6 +90,16 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// 16-byte asynchronous copy global -> shared, bypassing L1; zero-filled when
+// !valid (nothing is read then)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 __host__ __device__ constexpr int pad128(int b) { return (b + 127) / 128 * 128; }
 
@@ -409,7 +419,10 @@ __device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, f
 // ---------------------------------------------------------------------------
 // TAPE: also record, per interior node, the step's intermediates that the
 // adjoint reads (plane layout of the TapePlane enum, a.tape + plane * nx ny).
-template <int FORM, class ST, int NT, class SRC, bool TAPE = false, int TY = kTY>
+// OWN (one collision node per thread only): keep the own node's populations
+// in registers between the passes (below).
+template <int FORM, class ST, int NT, class SRC, bool TAPE = false, int TY = kTY,
+          bool OWN = kTX * TY == NT>
 __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, unsigned char* fs,
                                           int x0, int y0) {
   using F = Fields<FORM, TAPE, TY>;
@@ -417,6 +430,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   constexpr int N2 = F::N2, N1 = F::N1;
   constexpr int NPT = kTX * TY / NT;  // collision nodes per thread
   static_assert(kTX * TY % NT == 0, "whole collision nodes per thread");
+  // One collision node per thread (kOwn): the thread pulls its own node
+  // first in passes 1 and 3 and keeps those populations, and the node's
+  // force and velocity, in registers for pass 4, which then reads no plane;
+  // the ring nodes follow.  Same arithmetic per node as the row-major order.
+  static_assert(!OWN || NPT == 1, "own-node order needs one collision node per thread");
+  constexpr bool kOwn = OWN;
+  constexpr int NTILE = kTX * TY;
   // level-1 field slots in s2, ring-1 slots in s1
   constexpr int GX = 0, GY = 1, MU = 2, LAP = 3, E0 = F::kLap ? 4 : 3;
   constexpr int FX = 0, FY = 1, UX = 2, UY = 3, PUX = 4, PUY = 5;
@@ -450,13 +470,38 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   }
 
   // ---- pass 1: phi on tile + 3 ------------------------------------------------
-#pragma unroll 2
-  for (int k = tid; k < F::N3; k += NT) {
-    const int r = k / B3X, cc = k - r * B3X;
+  const auto phi_node = [&](int r, int cc) {
     const int yn = y0 - 3 + r;
-    if (!kIn && L.wall && (yn < 0 || yn >= L.ny)) continue;  // mirrored below
-    sPhi[k] = kIn ? src.phi(a, r, cc, x0 - 3 + cc, yn)
-                  : src.phi(a, r, cc, col(x0 - 3 + cc), L.wall ? yn : wrap(yn, L.ny));
+    if (!kIn && L.wall && (yn < 0 || yn >= L.ny)) return;  // mirrored below
+    sPhi[r * B3X + cc] = kIn ? src.phi(a, r, cc, x0 - 3 + cc, yn)
+                             : src.phi(a, r, cc, col(x0 - 3 + cc), L.wall ? yn : wrap(yn, L.ny));
+  };
+  // own node of the thread (kOwn): tile node (oly, olx)
+  const int oly = tid / kTX, olx = tid - oly * kTX;
+  const int ogx = x0 + olx, ogy = y0 + oly;
+  float hown[kOwn ? 9 : 1];
+  if constexpr (kOwn) {
+    if (kIn || !L.wall || ogy < L.ny) {
+      if constexpr (kIn) src.h_node(a, oly, olx, ogx, ogy, hown);
+      else src.h_node(a, oly, olx, col(ogx), L.wall ? ogy : wrap(ogy, L.ny), hown);
+      sPhi[(oly + 3) * B3X + olx + 3] = phi_sum<ST>(hown, P);
+    }
+    // the 3-ring: 3 rows above and below, then 3 columns left and right
+    for (int m = tid; m < F::N3 - NTILE; m += NT) {
+      if (m < 6 * B3X) {
+        const int rr = m / B3X;
+        phi_node(rr < 3 ? rr : rr + TY, m - rr * B3X);
+      } else {
+        const int q = (m - 6 * B3X) / 6, c6 = m - 6 * B3X - q * 6;
+        phi_node(3 + q, c6 < 3 ? c6 : kTX + c6);
+      }
+    }
+  } else {
+#pragma unroll 2
+    for (int k = tid; k < F::N3; k += NT) {
+      const int r = k / B3X;
+      phi_node(r, k - r * B3X);
+    }
   }
   __syncthreads();
   if (!kIn && L.wall && (y0 - 3 < 0 || y0 + TY + 3 > L.ny)) {
@@ -475,9 +520,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   // pass 2 so that a gather's latency overlaps it (16-bit planes, and the
   // STF-2 force's extra stencils, would spill the held values).  Box staging
   // takes the same order so that both modes round identically.
+  // kOwn: the held values are the own node's f (all nine, for pass 4).
   constexpr bool kPre = sizeof(typename ST::T) == 4 && FORM != kSTF2;
   float fpre[9];
-  if constexpr (kPre) {
+  const auto load_own_f = [&](float* f) {
+    if constexpr (kIn) src.f_node(a, oly, olx, ogx, ogy, f);
+    else src.f_node(a, oly, olx, col(ogx), map_row(ogy, L.ny, L.wall), f);
+  };
+  if constexpr (kPre && kOwn) {
+    load_own_f(fpre);
+  } else if constexpr (kPre) {
     const int ly = tid / B1X, lx = tid - ly * B1X;
     if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, fpre);
     else src.f_ring1(a, ly, lx, col(x0 - 1 + lx), map_row(y0 - 1 + ly, L.ny, L.wall), fpre);
@@ -509,7 +561,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
 
   // ---- pass 3: force, rho, u, phi u on tile + 1 -----------------------------
   static_assert(N1 > NT, "every thread has a first ring-1 node");
-  auto pass3 = [&](int k, const float* f) {
+  struct Node3 {
+    float Fx, Fy, ux, uy;
+  };
+  auto pass3 = [&](int k, const float* f) -> Node3 {
     const int ly = k / B1X, lx = k - ly * B1X;
     const int c2 = (ly + 1) * B2X + lx + 1;
     const float phi = sPhi[(ly + 2) * B3X + lx + 2];
@@ -570,8 +625,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const float irho = __fdividef(1.0f, rho);
     const float ux = (3.0f * jx + 0.5f * Fx) * irho;
     const float uy = (3.0f * jy + 0.5f * Fy) * irho;
-    s1[FX * N1 + k] = Fx;
-    s1[FY * N1 + k] = Fy;
+    if constexpr (!kOwn) {  // kOwn: pass 4 takes them from registers
+      s1[FX * N1 + k] = Fx;
+      s1[FY * N1 + k] = Fy;
+    }
     s1[UX * N1 + k] = ux;
     s1[UY * N1 + k] = uy;
     s1[PUX * N1 + k] = phi * ux;
@@ -588,17 +645,39 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
         t[TP_UY * nn] = uy;
       }
     }
+    return Node3{Fx, Fy, ux, uy};
   };
   auto load_ring1 = [&](int k, float* f) {
     const int ly = k / B1X, lx = k - ly * B1X;
     if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, f);
     else src.f_ring1(a, ly, lx, col(x0 - 1 + lx), map_row(y0 - 1 + ly, L.ny, L.wall), f);
   };
-  if constexpr (kPre) pass3(tid, fpre);
-  for (int k = kPre ? tid + NT : tid; k < N1; k += NT) {
-    float f[9];
-    load_ring1(k, f);
-    pass3(k, f);
+  Node3 own3{};
+  if constexpr (kOwn) {
+    if constexpr (!kPre) load_own_f(fpre);
+    own3 = pass3((oly + 1) * B1X + olx + 1, fpre);
+    // the 1-ring: the rows above and below, then the columns left and right
+    for (int m = tid; m < N1 - NTILE; m += NT) {
+      int ly1, lx1;
+      if (m < 2 * B1X) {
+        ly1 = m < B1X ? 0 : TY + 1;
+        lx1 = m < B1X ? m : m - B1X;
+      } else {
+        const int q = m - 2 * B1X;
+        ly1 = 1 + (q >> 1);
+        lx1 = (q & 1) ? kTX + 1 : 0;
+      }
+      float f[9];
+      load_ring1(ly1 * B1X + lx1, f);
+      pass3(ly1 * B1X + lx1, f);
+    }
+  } else {
+    if constexpr (kPre) pass3(tid, fpre);
+    for (int k = kPre ? tid + NT : tid; k < N1; k += NT) {
+      float f[9];
+      load_ring1(k, f);
+      pass3(k, f);
+    }
   }
   __syncthreads();
 
@@ -662,13 +741,20 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     const float phi = sPhi[(ly + 3) * B3X + lx + 3];
     const float Gx = s2[GX * N2 + c2], Gy = s2[GY * N2 + c2];
     const float mu = s2[MU * N2 + c2];
-    const float Fx = s1[FX * N1 + c1], Fy = s1[FY * N1 + c1];
-    const float ux = s1[UX * N1 + c1], uy = s1[UY * N1 + c1];
+    const float Fx = kOwn ? own3.Fx : s1[FX * N1 + c1];
+    const float Fy = kOwn ? own3.Fy : s1[FY * N1 + c1];
+    const float ux = kOwn ? own3.ux : s1[UX * N1 + c1];
+    const float uy = kOwn ? own3.uy : s1[UY * N1 + c1];
     const float rho = P.rho_mid + P.drho_half * phi;
     const float drx = P.drho_half * Gx, dry = P.drho_half * Gy;
 
     float f[9];
-    src.f_node(a, ly, lx, gx, gy, f);
+    if constexpr (kOwn) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = fpre[i];
+    } else {
+      src.f_node(a, ly, lx, gx, gy, f);
+    }
     const float sumf = f_sum<ST>(f, P);
     // Eq. mac: P = sum f + cs^2/2 u . grad rho
     const float Pr = sumf + (ux * drx + uy * dry) * (1.0f / 6.0f);
@@ -728,7 +814,12 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     }
 
     float h[9];
-    src.h_node(a, ly, lx, gx, gy, h);
+    if constexpr (kOwn) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = hown[i];
+    } else {
+      src.h_node(a, ly, lx, gx, gy, h);
+    }
 
     // relaxation: tau_f = 1/2 + mu(phi) / (cs^2 rho) (Sec. 3)
     const float mv = P.mu_mid + P.mu_dhalf * phi;
@@ -912,16 +1003,36 @@ __global__ void __launch_bounds__(kThreadsBoxes, kBlocksBoxes)
 
 // kGather: one CTA per tile, populations gathered through L1.  XW: free-slip
 // side walls (a separate instantiation, so periodic domains run unchanged code).
-template <int FORM, class ST, bool XW>
-__global__ void __launch_bounds__(kThreadsGather, kBlocksGather)
-    k_step_gather(const __grid_constant__ StepArgs a) {
+// NT threads per 32 x TY tile, MINB CTAs per SM: kGather runs 32 x 16 tiles
+// (two collision nodes per thread), kGather8 32 x 8 tiles (one, own-node
+// order).
+template <int FORM, class ST, bool XW, int NT, int TY, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step_gather(const __grid_constant__ StepArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
   const int ntx = (a.L.nx + kTX - 1) / kTX;
-  const int x0 = (blockIdx.x % ntx) * kTX, y0 = (blockIdx.x / ntx) * kTY;
-  if (inner_tile(a.L, x0, y0))
-    step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, true>{}, sm, x0, y0);
+  const int x0 = (blockIdx.x % ntx) * kTX, y0 = (blockIdx.x / ntx) * TY;
+  if (inner_tile<TY>(a.L, x0, y0))
+    step_tile<FORM, ST, NT, GatherSrc<ST, true>, false, TY>(a, GatherSrc<ST, true>{}, sm, x0, y0);
   else
-    step_tile<FORM, ST, kThreadsGather>(a, GatherSrc<ST, false, XW>{}, sm, x0, y0);
+    step_tile<FORM, ST, NT, GatherSrc<ST, false, XW>, false, TY>(a, GatherSrc<ST, false, XW>{},
+                                                                 sm, x0, y0);
+}
+template <int FORM, class ST, int NT, int TY, int MINB>
+cudaError_t launch_gather(const StepArgs& a, cudaStream_t s, bool& configured) {
+  constexpr int kBytes = Fields<FORM, false, TY>::BYTES;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_gather<FORM, ST, false, NT, TY, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_step_gather<FORM, ST, true, NT, TY, MINB>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int ntiles = ((a.L.nx + kTX - 1) / kTX) * ((a.L.ny + TY - 1) / TY);
+  if (a.L.wall_x) k_step_gather<FORM, ST, true, NT, TY, MINB><<<ntiles, NT, kBytes, s>>>(a);
+  else k_step_gather<FORM, ST, false, NT, TY, MINB><<<ntiles, NT, kBytes, s>>>(a);
+  return cudaGetLastError();
 }
 
 // Taping step of the adjoint's recomputation (float32 storage, gathers): the
@@ -950,31 +1061,22 @@ template <int FORM, class ST>
 cudaError_t launch_form(int mode, const StepArgs& a, cudaStream_t s) {
   // the macroscopic read-back always takes the tile kernels
   if (mode == kMarch && !a.macro) return launch_march<FORM, ST>(a, s);
-  static bool configured = false;  // per instantiation; attributes are per function
+  static bool cfg[2] = {false, false};  // per instantiation and tile height
+  if (mode == kGather8)
+    return launch_gather<FORM, ST, kThreadsGather, kShortRows, kBlocksGather>(a, s, cfg[1]);
+  if (mode != kBoxes)
+    return launch_gather<FORM, ST, kThreadsGather, kTY, kBlocksGather>(a, s, cfg[0]);
+  static bool configured = false;
   constexpr int kBoxBytes = 128 + Boxes<ST>::BYTES + Fields<FORM>::BYTES;
-  constexpr int kGatherBytes = Fields<FORM>::BYTES;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_step_boxes<FORM, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step_gather<FORM, ST, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, kGatherBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_step_gather<FORM, ST, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, kGatherBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const int ntiles = ((a.L.nx + kTX - 1) / kTX) * ((a.L.ny + kTY - 1) / kTY);
-  if (mode == kBoxes) {
-    const int slots = num_sms() * kBlocksBoxes;
-    k_step_boxes<FORM, ST><<<ntiles < slots ? ntiles : slots, kThreadsBoxes, kBoxBytes, s>>>(a);
-  } else {
-    if (a.L.wall_x)
-      k_step_gather<FORM, ST, true><<<ntiles, kThreadsGather, kGatherBytes, s>>>(a);
-    else
-      k_step_gather<FORM, ST, false><<<ntiles, kThreadsGather, kGatherBytes, s>>>(a);
-  }
+  const int slots = num_sms() * kBlocksBoxes;
+  k_step_boxes<FORM, ST><<<ntiles < slots ? ntiles : slots, kThreadsBoxes, kBoxBytes, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -193,7 +193,7 @@ def pflbm_set_tma(d, enable: bool):
     _check(load().pflbm_set_tma(d, int(bool(enable))), "pflbm_set_tma")
 
 
-STAGE_MODES = {"boxes": 0, "gather": 1, "march": 2}
+STAGE_MODES = {"boxes": 0, "gather": 1, "march": 2, "gather8": 3}
 
 
 def pflbm_set_stage_mode(d, mode: int):
