@@ -87,7 +87,8 @@ def test_side_walls_refuse_x_forcing_and_boxes(pf):
     with pytest.raises(pf.PflbmError):
         d.stage_mode("boxes")
     d.init_phi(wl.drop(40, 40, 8.0, 4.0, periodic_y=False).astype(np.float32))
-    assert d.autotune(2) == "gather"
+    # side walls are staged by gathers (32 x 16 or 32 x 8 tiles) only
+    assert d.autotune(2) in ("gather", "gather8")
 
 
 @pytest.mark.parametrize("storage,tol_phi,tol_u", [("fp16", 2e-4, 2e-5), ("bf16", 2e-3, 2e-4)])
