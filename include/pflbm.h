@@ -319,13 +319,14 @@ pflbm_status pflbm_adjoint_run(pflbm_domain* d, const float* phi0, int nsteps, i
 typedef struct pflbm_batch pflbm_batch;
 
 /* Device scratch a batch of these n domains needs: two argument records per
- * domain and one work item per (domain, tile). */
+ * domain, one work item per (domain, tile) and the kernel's item counter. */
 size_t pflbm_batch_workspace_bytes(int n, pflbm_domain* const* doms);
 
 /* Group n domains (FP32 storage, parameters and initial state set; sizes and
  * force forms may all differ) into a batch whose steps run on cuda_stream.
- * Each step is ONE persistent launch: CTAs walk a work-list of (domain,
- * tile) items sorted by force form.  The domains keep their own state and
+ * Each step is ONE persistent launch: CTAs claim (domain, tile) items of a
+ * work-list sorted by force form from a counter in the workspace, which the
+ * step zeroes on cuda_stream before the launch.  The domains keep their own state and
  * remain usable one by one (diagnostics, read-back) once the batch stream
  * has been synchronised; stepping a domain alone between batch steps is
  * allowed.  The batch keeps the domain handles and the workspace until

@@ -119,12 +119,18 @@ __device__ __forceinline__ void acc_add(double* acc, double v0, double v1, doubl
 #define AI(pl) (A.ain + (size_t)(kAdjScalar + (pl)) * n)
 #define AO(pl) (A.aout + (size_t)(kAdjScalar + (pl)) * n)
 // element m of a plane, the offset formed in 32 bits (the host refuses grids
-// whose planes would reach 2^31 elements)
-#define TPK(pl, m) (A.tape[(unsigned)((pl) * n + (m))])
-#define AIK(pl, m) (A.ain[(unsigned)((kAdjScalar + (pl)) * n + (m))])
+// whose planes would reach 2^31 elements).  The tape and the incoming adjoint
+// state are never written by a reverse kernel, and a work plane is read by a
+// kernel only where that kernel does not write it (or by the thread that
+// writes it, before the write): such reads take the read-only path
+// (ld.global.nc), which lets the compiler issue them ahead of the stores of
+// earlier directions instead of after them.
+#define TPK(pl, m) (__ldg(A.tape + (unsigned)((pl) * n + (m))))
+#define AIK(pl, m) (__ldg(A.ain + (unsigned)((kAdjScalar + (pl)) * n + (m))))
 #define AOK(pl, m) (A.aout[(unsigned)((kAdjScalar + (pl)) * n + (m))])
 #define WKK(pl, m) (A.W[(unsigned)((pl) * n + (m))])
-#define SI(m) (reinterpret_cast<const float4*>(A.ain)[m])
+#define WKR(pl, m) (__ldg(A.W + (unsigned)((pl) * n + (m))))
+#define SI(m) (__ldg(reinterpret_cast<const float4*>(A.ain) + (m)))
 #define SO(m) (reinterpret_cast<float4*>(A.aout)[m])
 #define WK(pl) (A.W + (size_t)(pl) * n)
 
@@ -265,7 +271,7 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
   float pxb = stencil_T<false>(divb, g, x, y, 0, -1.0f);
   float pyb = stencil_T<false>(divb, g, x, y, 1, -1.0f);
   Tail o;
-  o.phib = WKK(B_PHI, k);
+  o.phib = WKR(B_PHI, k);
   if (g.wall && (y == 0 || y == g.ny - 1)) {
     // ghost adjoint of p_x at (x, -1) or (x, ny): nodes of this row whose
     // stencil reads it; its 2 u_w phi(x, row) part goes to phi
@@ -278,7 +284,7 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
   }
   pxb += AIK(AP_QX, k);
   pyb += AIK(AP_QY, k);
-  const float dtxb = A.first ? 0.0f : WKK(B_DTX, k), dtyb = A.first ? 0.0f : WKK(B_DTY, k);
+  const float dtxb = A.first ? 0.0f : WKR(B_DTX, k), dtyb = A.first ? 0.0f : WKR(B_DTY, k);
   pxb += dtxb;
   pyb += dtyb;
   // macroscopic relations
@@ -288,25 +294,25 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
   const float rho = P.rho_mid + P.drho_half * phi;
   const float irho = 1.0f / rho;
   const float Rx = P.drho_half * gx, Ry = P.drho_half * gy;
-  const float Pb = WKK(B_P, k);
+  const float Pb = WKR(B_P, k);
   o.phib += pxb * ux + pyb * uy;
-  const float uxb = WKK(B_UX, k) + phi * pxb + Rx * c6 * Pb;
-  const float uyb = WKK(B_UY, k) + phi * pyb + Ry * c6 * Pb;
-  o.Gxb = WKK(B_GX, k) + P.drho_half * (ux * c6 * Pb);
-  o.Gyb = WKK(B_GY, k) + P.drho_half * (uy * c6 * Pb);
+  const float uxb = WKR(B_UX, k) + phi * pxb + Rx * c6 * Pb;
+  const float uyb = WKR(B_UY, k) + phi * pyb + Ry * c6 * Pb;
+  o.Gxb = WKR(B_GX, k) + P.drho_half * (ux * c6 * Pb);
+  o.Gyb = WKR(B_GY, k) + P.drho_half * (uy * c6 * Pb);
   if (own) {
     AOK(AP_QX, k) = -dtxb;
     AOK(AP_QY, k) = -dtyb;
     // (PHI, the w component, is written by the finishing stage)
     SO(k) = make_float4(Pb, 3.0f * uxb * irho, 3.0f * uyb * irho, 0.0f);
   }
-  const float Fxb = WKK(B_FX, k) + 0.5f * uxb * irho;  // adjoint of F_sf
-  const float Fyb = WKK(B_FY, k) + 0.5f * uyb * irho;
-  float rhob = WKK(B_RHO, k) - (ux * uxb + uy * uyb) * irho;
+  const float Fxb = WKR(B_FX, k) + 0.5f * uxb * irho;  // adjoint of F_sf
+  const float Fyb = WKR(B_FY, k) + 0.5f * uyb * irho;
+  float rhob = WKR(B_RHO, k) - (ux * uxb + uy * uyb) * irho;
   rhob += P.gx * Fxb + P.gy * Fyb;
   o.phib += P.drho_half * rhob;
   // pointwise part of the force
-  o.mub = WKK(B_MU, k);
+  o.mub = WKR(B_MU, k);
   o.Lb = o.w0 = o.w1 = o.w2 = 0.0f;
   const float a0 = TPK(TP_A0, k), a1 = TPK(TP_A1, k);
   switch (A.form) {

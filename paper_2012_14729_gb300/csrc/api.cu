@@ -1065,6 +1065,7 @@ struct pflbm_batch {
   size_t table_off;
   // work-lists for tiles of kTY rows ([0]) and of kShortRows rows ([1])
   size_t items_off[2];
+  size_t tickets_off;  // the batch kernel's item counter
   int nitems[2];
   int mode, ctas_per_sm, rows;
   int graphs;
@@ -1117,7 +1118,8 @@ cudaError_t batch_launch(const pflbm_batch* b, int bp) {
   const int r = rows_slot(b->rows);
   return launch_batch(b->mode, b->rows, reinterpret_cast<const StepArgs*>(b->ws + b->table_off),
                       reinterpret_cast<const int4*>(b->ws + b->items_off[r]), b->nitems[r], bp,
-                      batch_grid(b), b->stream);
+                      batch_grid(b), reinterpret_cast<unsigned*>(b->ws + b->tickets_off),
+                      b->stream);
 }
 
 }  // namespace
@@ -1135,7 +1137,7 @@ size_t pflbm_batch_workspace_bytes(int n, pflbm_domain* const* doms) {
     }
     bytes += align_up(sizeof(int4) * (size_t)items);
   }
-  return bytes;
+  return bytes + align_up(sizeof(unsigned));  // the item counter
 }
 
 pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_workspace,
@@ -1199,6 +1201,7 @@ pflbm_status pflbm_batch_create(int n, pflbm_domain* const* doms, void* dev_work
     b->items_off[r] = off;
     b->nitems[r] = (int)k;
     off += align_up(sizeof(int4) * (size_t)k);
+    b->tickets_off = off;
     cudaError_t e = cudaMemcpyAsync(b->ws + b->items_off[r], h, sizeof(int4) * k,
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -1,6 +1,8 @@
 // Batched step: many independent domains of uneven sizes and force forms
-// advance together, one persistent launch per time step.  The CTAs walk a
-// work-list of (instance, tile) items sorted by force form; each item runs
+// advance together, one persistent launch per time step.  The CTAs take
+// (instance, tile) items of a work-list sorted by force form from a ticket
+// counter (the next unclaimed item goes to whichever CTA asks first, so that
+// the CTAs finish together although items differ in cost); each item runs
 // the same per-tile passes as the single-domain kernels, with the instance's
 // arguments taken from a table in global memory (FP32 storage).  Gather-mode
 // batches run tiles of kTY or kShortRows rows (two or one collision nodes
@@ -71,20 +73,24 @@ struct BatchCfg<kBoxes> {
 template <>
 struct BatchCfg<kGather> {
   // four resident CTAs like the single-domain gather kernel: measured faster
-  // on 256 instances (18.7 vs 17.6 GLUPS) than three CTAs with 85 registers,
+  // on 256 instances (24.4 vs 21.2 GLUPS with claimed items) than three,
   // although the item loop and form dispatch then spill a few registers
   static constexpr int NT = kThreadsGather, MINB = kBlocksGather;
 };
 
+// `tickets` counts the items claimed in this launch (zero at its start).
 template <class ST, int MODE, int TY>
 __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
     k_step_batch(const StepArgs* __restrict__ table, const int4* __restrict__ items, int nitems,
-                 int bp) {
+                 int bp, unsigned* __restrict__ tickets) {
   constexpr int NT = BatchCfg<MODE>::NT;
   constexpr bool kAsync = sizeof(typename ST::T) == 4;
   extern __shared__ __align__(128) unsigned char sm[];
   // the arguments of this item and of the next one (two buffers)
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kArgsBytes);
+  // the item indices of the two buffers (slot p: the item whose arguments
+  // buffer p receives next)
+  int* slot = reinterpret_cast<int*>(sm + 2 * kArgsBytes + 8);
   // the descriptors of this item and of the next one (two slots)
   int4* desc = reinterpret_cast<int4*>(sm + 2 * kArgsBytes + 16);
   unsigned char* bx = sm + 2 * kArgsBytes + 128;
@@ -112,17 +118,42 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
     }
   }
   uint32_t parity = 0u;
-  copy_args(blockIdx.x, 0);
+  // claim a ticket: the index of an unclaimed item (>= nitems: none left)
+  const auto claim = [&]() { return (int)min(atomicAdd(tickets, 1u), (unsigned)nitems); };
+  // the same, stored straight into a shared-memory slot (one asm block, so
+  // that no register holds the ticket across the item's passes)
+  const auto claim_into = [&](int* dst) {
+    asm volatile(
+        "{\n .reg .u32 t;\n atom.global.add.u32 t, [%0], 1;\n min.u32 t, t, %2;\n"
+        " st.shared.u32 [%1], t;\n}" ::"l"(tickets),
+        "r"(smem_addr(dst)), "r"((unsigned)nitems)
+        : "memory");
+  };
+  if (threadIdx.x == 0) slot[0] = claim();
+  __syncthreads();
+  int it = slot[0];
+  copy_args(it, 0);
+  // the item after it, published by the barrier at the top of the loop
+  if (threadIdx.x == 0) slot[1] = claim();
   int buf = 0;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x, buf ^= 1) {
-    // this item's arguments and descriptor are in place, and every thread
-    // is done with the other buffer and slot (the previous item's): fill
-    // them with the next item's
+  while (it < nitems) {
+    // this item's arguments and descriptor are in place, the next item's
+    // index is in slot[buf ^ 1], and every thread is done with the other
+    // buffer and slot (the previous item's): fill them with the next item's
     cp_async_wait_all();
     __syncthreads();
+    const int next = slot[buf ^ 1];
+    // the item after `next`, claimed now so that the atomic's round trip
+    // overlaps the other warps' start of this item; slot[buf] was last read
+    // before the barrier above (as this item's index), and the barrier at the
+    // top of the next iteration publishes it
+    if (threadIdx.x == 0) {
+      if (next < nitems) claim_into(&slot[buf]);
+      else slot[buf] = nitems;
+    }
     const int4 item = desc[buf];
     const StepArgs& ga = table[2 * item.x + bp];
-    copy_args(it + gridDim.x, buf ^ 1);
+    copy_args(next, buf ^ 1);
     const StepArgs& a = *reinterpret_cast<const StepArgs*>(sm + buf * kArgsBytes);
     const int x0 = item.y, y0 = item.z;
     if constexpr (MODE == kBoxes) {
@@ -138,6 +169,8 @@ __global__ void __launch_bounds__(BatchCfg<MODE>::NT, BatchCfg<MODE>::MINB)
       }
     }
     run_item<ST, MODE, NT, TY>(a, ga, item.w, bx, fs, x0, y0);
+    it = next;
+    buf ^= 1;
   }
 }
 
@@ -148,7 +181,7 @@ constexpr int batch_smem() {
 
 template <int MODE, int TY>
 cudaError_t launch_batch_mode(const StepArgs* table, const int4* items, int nitems, int bp,
-                              int grid, cudaStream_t s) {
+                              int grid, unsigned* tickets, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_step_batch<StoreF32, MODE, TY>,
@@ -157,8 +190,11 @@ cudaError_t launch_batch_mode(const StepArgs* table, const int4* items, int nite
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  // the launch claims its items from a zeroed counter
+  cudaError_t e = cudaMemsetAsync(tickets, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
   k_step_batch<StoreF32, MODE, TY><<<grid, BatchCfg<MODE>::NT, batch_smem<MODE>(), s>>>(
-      table, items, nitems, bp);
+      table, items, nitems, bp, tickets);
   return cudaGetLastError();
 }
 
@@ -169,15 +205,15 @@ int batch_blocks_per_sm(int mode) {
 }
 
 cudaError_t launch_batch(int mode, int rows, const StepArgs* table, const int4* items,
-                         int nitems, int bp, int grid, cudaStream_t s) {
+                         int nitems, int bp, int grid, unsigned* tickets, cudaStream_t s) {
   if (mode == kBoxes) {
     if (rows != kTY) return cudaErrorInvalidValue;
-    return launch_batch_mode<kBoxes, kTY>(table, items, nitems, bp, grid, s);
+    return launch_batch_mode<kBoxes, kTY>(table, items, nitems, bp, grid, tickets, s);
   }
   if (rows == kShortRows)
-    return launch_batch_mode<kGather, kShortRows>(table, items, nitems, bp, grid, s);
+    return launch_batch_mode<kGather, kShortRows>(table, items, nitems, bp, grid, tickets, s);
   if (rows != kTY) return cudaErrorInvalidValue;
-  return launch_batch_mode<kGather, kTY>(table, items, nitems, bp, grid, s);
+  return launch_batch_mode<kGather, kTY>(table, items, nitems, bp, grid, tickets, s);
 }
 
 }  // namespace pflbm

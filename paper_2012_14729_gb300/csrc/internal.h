@@ -151,11 +151,13 @@ cudaError_t launch_adjoint_init(const AdjArgs& A, const float* phi0, float* dphi
 // Batched step over a work-list (batch.cu): table holds 2 StepArgs per
 // instance (entry 2 i + p reads buffer cur_i ^ p), items (instance, x0, y0,
 // form) for tiles of `rows` rows (kTY, or kShortRows in the gather mode);
-// `bp` is the step parity; `grid` persistent CTAs.
+// `bp` is the step parity; `grid` persistent CTAs, which claim the items
+// through the device counter `tickets` (zeroed on the stream before the
+// kernel).
 int batch_blocks_per_sm(int mode);
 int num_sms();  // streaming multiprocessors of the current device
 cudaError_t launch_batch(int mode, int rows, const StepArgs* table, const int4* items,
-                         int nitems, int bp, int grid, cudaStream_t s);
+                         int nitems, int bp, int grid, unsigned* tickets, cudaStream_t s);
 
 cudaError_t launch_step_fp32(int form, int mode, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp16(int form, int mode, const StepArgs& a, cudaStream_t s);
