@@ -62,7 +62,9 @@ __device__ __forceinline__ float lapfw(const float* a, const Geo& g, int x, int 
 // Transpose of dfw: sum over the nodes x' whose stencil reads node (x, y),
 // directly or through a ghost, of coef_i * b(x').  `wcoef` selects the
 // weights: 3 w_i c_i,axis (derivative) or 6 w_i (Laplacian neighbour part).
-template <bool LAP>
+// IN: the node and the nodes its transpose reads lie inside the domain, off
+// the wall rows and away from the periodic seams (no wrap, no ghost term).
+template <bool LAP, bool IN = false>
 __device__ __forceinline__ float stencil_T(const float* b, const Geo& g, int x, int y, int axis,
                                            float parity) {
   float s = 0.0f;
@@ -71,6 +73,10 @@ __device__ __forceinline__ float stencil_T(const float* b, const Geo& g, int x, 
     const int c = LAP ? 1 : (axis == 0 ? qcx(i) : qcy(i));
     if (c == 0) continue;
     const float coef = LAP ? 6.0f * qw(i) : 3.0f * qw(i) * c;
+    if constexpr (IN) {
+      s += coef * b[(y - qcy(i)) * g.nx + x - qcx(i)];
+      continue;
+    }
     const int xs = wx(g, x - qcx(i));
     int ys = y - qcy(i);
     if (g.wall) {
@@ -261,6 +267,7 @@ struct Tail {
 // rho(phi), and the pointwise part of the force of the form; leaves in
 // w0..w2 what the force's stencil transposes read.  The node's outputs to the
 // adjoint state (q and the scalar block) are written when `own`.
+template <bool IN = false>
 __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, int k, bool own,
                                          double& dk, double& ds) {
   const Phys& P = A.p;
@@ -268,11 +275,11 @@ __device__ __forceinline__ Tail mid_node(const AdjArgs& A, int n, int x, int y, 
   const float* divb = WK(B_DIV);
   // p_x is read as parity -1 with an additive 2 u_w phi at the wall ghosts,
   // p_y with parity -1; periodic wraps
-  float pxb = stencil_T<false>(divb, g, x, y, 0, -1.0f);
-  float pyb = stencil_T<false>(divb, g, x, y, 1, -1.0f);
+  float pxb = stencil_T<false, IN>(divb, g, x, y, 0, -1.0f);
+  float pyb = stencil_T<false, IN>(divb, g, x, y, 1, -1.0f);
   Tail o;
   o.phib = WKR(B_PHI, k);
-  if (g.wall && (y == 0 || y == g.ny - 1)) {
+  if (!IN && g.wall && (y == 0 || y == g.ny - 1)) {
     // ghost adjoint of p_x at (x, -1) or (x, ny): nodes of this row whose
     // stencil reads it; its 2 u_w phi(x, row) part goes to phi
     const int cyw = y == 0 ? -1 : 1;
@@ -425,7 +432,7 @@ __device__ __forceinline__ void late_node(const AdjArgs& A, int n, int k, Tail& 
 // Transposed stencils on a shared-memory tile of row stride S: node at local
 // index c, domain row y (the wall rule of stencil_T, periodic seams already
 // resolved by the tile's layout).
-template <bool LAP, int S>
+template <bool LAP, int S, bool IN = false>
 __device__ __forceinline__ float stencil_T_tile(const float* b, int c, int y, const Geo& g,
                                                 int axis, float parity) {
   float s = 0.0f;
@@ -435,7 +442,7 @@ __device__ __forceinline__ float stencil_T_tile(const float* b, int c, int y, co
     const int cc = LAP ? 1 : (axis == 0 ? cxi : cyi);
     if (cc == 0) continue;
     const float coef = LAP ? 6.0f * qw(i) : 3.0f * qw(i) * cc;
-    if (g.wall) {
+    if (!IN && g.wall) {
       const int ys = y - cyi;
       if (ys >= 0 && ys < g.ny) s += coef * b[c - cxi - cyi * S];
       if ((y == 0 && cyi == -1) || (y == g.ny - 1 && cyi == 1)) s += parity * coef * b[c - cxi];
@@ -452,17 +459,25 @@ __device__ __forceinline__ float stencil_T_tile(const float* b, int c, int y, co
 // (its stencils read the middle stage's w0..w2 in shared memory), the
 // finishing transposes of grad phi and lap phi on the tile.  A ring node
 // outside the domain beyond a wall is skipped (no stencil reads it); every
-// parameter gradient term comes from the tile's own nodes.
+// parameter gradient term comes from the tile's own nodes.  IN: the tile + 3
+// ring lies inside the domain, off the wall rows and the periodic seams (no
+// wrap, no ghost terms).
 constexpr int kTW = 32, kTH = 8, kTS = kTW + 4, kTN = kTS * (kTH + 4);
-__global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
+// 256 threads, six CTAs per SM (40 registers): measured faster than one
+// thread per ring node (448 threads, three or four CTAs per SM)
+constexpr int kTailThreads = 256, kTailBlocks = 6;
+template <bool IN>
+__device__ __forceinline__ void tail_tile(const AdjArgs& A, float (*sw)[kTN], float (*sv)[kTN],
+                                          int x0, int y0, double& db, double& dk, double& ds) {
   const int n = A.g.nx * A.g.ny;
   const Geo& g = A.g;
-  __shared__ float sw[3][kTN];   // w0, w1, w2
-  __shared__ float sv[5][kTN];   // phib, Gxb, Gyb, mub, Lb
-  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-  double dk = 0.0, ds = 0.0, db = 0.0;
   // node (lx, ly) of the tile + 2 ring: domain coordinates, or false beyond a wall
   auto node = [&](int lx, int ly, int& x, int& y) {
+    if constexpr (IN) {
+      x = x0 - 2 + lx;
+      y = y0 - 2 + ly;
+      return true;
+    }
     x = wx(g, x0 - 2 + lx);
     y = y0 - 2 + ly;
     if (g.wall) return y >= 0 && y < g.ny;
@@ -470,16 +485,16 @@ __global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
     return true;
   };
   auto owned = [&](int lx, int ly) {
-    return lx >= 2 && lx < kTW + 2 && ly >= 2 && ly < kTH + 2 && x0 + lx - 2 < g.nx &&
-           y0 + ly - 2 < g.ny;
+    return lx >= 2 && lx < kTW + 2 && ly >= 2 && ly < kTH + 2 &&
+           (IN || (x0 + lx - 2 < g.nx && y0 + ly - 2 < g.ny));
   };
-  for (int c = threadIdx.x; c < kTN; c += 256) {
+  for (int c = threadIdx.x; c < kTN; c += kTailThreads) {
     const int ly = c / kTS, lx = c - ly * kTS;
     int x, y;
     if (!node(lx, ly, x, y)) continue;
     const bool own = owned(lx, ly);
     double dkn = 0.0, dsn = 0.0;
-    const Tail t = mid_node(A, n, x, y, y * g.nx + x, own, dkn, dsn);
+    const Tail t = mid_node<IN>(A, n, x, y, y * g.nx + x, own, dkn, dsn);
     if (own) {
       dk += dkn;
       ds += dsn;
@@ -494,7 +509,7 @@ __global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
     sv[4][c] = t.Lb;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < kTN; c += 256) {
+  for (int c = threadIdx.x; c < kTN; c += kTailThreads) {
     const int ly = c / kTS, lx = c - ly * kTS;
     if (lx < 1 || lx > kTW + 2 || ly < 1 || ly > kTH + 2) continue;  // tile + 1 ring
     int x, y;
@@ -506,7 +521,7 @@ __global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
     v.mub = sv[3][c];
     v.Lb = sv[4][c];
     const auto st = [&](int f, int axis, float parity) {
-      return stencil_T_tile<false, kTS>(sw[f], c, y, g, axis, parity);
+      return stencil_T_tile<false, kTS, IN>(sw[f], c, y, g, axis, parity);
     };
     double dbn = 0.0, dkn = 0.0;
     late_node(A, n, y * g.nx + x, v, st, dbn, dkn);
@@ -520,19 +535,32 @@ __global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
     sv[4][c] = v.Lb;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < kTN; c += 256) {
+  for (int c = threadIdx.x; c < kTN; c += kTailThreads) {
     const int ly = c / kTS, lx = c - ly * kTS;
     if (!owned(lx, ly)) continue;
     int x, y;
     node(lx, ly, x, y);
     const int k = y * g.nx + x;
     reinterpret_cast<float*>(A.aout)[4 * k + 3] =  // the PHI (w) component of SO(k)
-        sv[0][c] + stencil_T_tile<false, kTS>(sv[1], c, y, g, 0, 1.0f) +
-        stencil_T_tile<false, kTS>(sv[2], c, y, g, 1, 1.0f) +
-        stencil_T_tile<true, kTS>(sv[4], c, y, g, 0, 1.0f);
+        sv[0][c] + stencil_T_tile<false, kTS, IN>(sv[1], c, y, g, 0, 1.0f) +
+        stencil_T_tile<false, kTS, IN>(sv[2], c, y, g, 1, 1.0f) +
+        stencil_T_tile<true, kTS, IN>(sv[4], c, y, g, 0, 1.0f);
   }
-  // one FP64 block reduction of the four accumulators (256 threads)
-  __shared__ double red[8][4];
+}
+
+__global__ void __launch_bounds__(kTailThreads, kTailBlocks) k_adj_tail(const AdjArgs A) {
+  const Geo& g = A.g;
+  __shared__ float sw[3][kTN];   // w0, w1, w2
+  __shared__ float sv[5][kTN];   // phib, Gxb, Gyb, mub, Lb
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+  double dk = 0.0, ds = 0.0, db = 0.0;
+  // the middle stage's divergence transpose reads the tile + 3 ring
+  const bool in = x0 >= 3 && x0 + kTW + 3 <= g.nx && y0 >= 3 && y0 + kTH + 3 <= g.ny;
+  if (in) tail_tile<true>(A, sw, sv, x0, y0, db, dk, ds);
+  else tail_tile<false>(A, sw, sv, x0, y0, db, dk, ds);
+  // one FP64 block reduction of the four accumulators
+  constexpr int kWarps = kTailThreads / 32;
+  __shared__ double red[kWarps][4];
   double v4[4] = {db, dk, 0.0, ds};
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -545,7 +573,7 @@ __global__ void __launch_bounds__(256) k_adj_tail(const AdjArgs A) {
   __syncthreads();
   if (threadIdx.x < 4) {
     double s = 0.0;
-    for (int j = 0; j < 8; ++j) s += red[j][threadIdx.x];
+    for (int j = 0; j < kWarps; ++j) s += red[j][threadIdx.x];
     if (s != 0.0) atomicAdd(&A.acc[threadIdx.x], s);
   }
 }
@@ -618,7 +646,7 @@ cudaError_t launch_adjoint_step(const AdjArgs& A, cudaStream_t s) {
   k_adj_collide<<<grid, kAB, 0, s>>>(A);
   if ((long long)A.g.nx * A.g.ny <= kTailFusedMaxNodes) {
     const dim3 tiles((A.g.nx + kTW - 1) / kTW, (A.g.ny + kTH - 1) / kTH);
-    k_adj_tail<<<tiles, 256, 0, s>>>(A);
+    k_adj_tail<<<tiles, kTailThreads, 0, s>>>(A);
   } else {
     k_adj_mid<<<grid, kAB, 0, s>>>(A);
     k_adj_late<<<grid, kAB, 0, s>>>(A);
