@@ -487,13 +487,35 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       sPhi[(oly + 3) * B3X + olx + 3] = phi_sum<ST>(hown, P);
     }
     // the 3-ring: 3 rows above and below, then 3 columns left and right
-    for (int m = tid; m < F::N3 - NTILE; m += NT) {
+    const auto ring3 = [&](int m, int& r, int& cc) {
       if (m < 6 * B3X) {
         const int rr = m / B3X;
-        phi_node(rr < 3 ? rr : rr + TY, m - rr * B3X);
+        r = rr < 3 ? rr : rr + TY;
+        cc = m - rr * B3X;
       } else {
         const int q = (m - 6 * B3X) / 6, c6 = m - 6 * B3X - q * 6;
-        phi_node(3 + q, c6 < 3 ? c6 : kTX + c6);
+        r = 3 + q;
+        cc = c6 < 3 ? c6 : kTX + c6;
+      }
+    };
+    constexpr int R3 = F::N3 - NTILE;
+    if constexpr (kIn && R3 <= 2 * NT) {
+      // at most two ring nodes per thread: both pulls are issued before
+      // either sum, so that the CTA waits for one round of loads, not two
+      const bool v1 = R3 >= NT || tid < R3, v2 = tid + NT < R3;
+      int r1, c1, r2, c2;
+      ring3(v1 ? tid : 0, r1, c1);
+      ring3(v2 ? tid + NT : 0, r2, c2);
+      float p1 = 0.0f, p2 = 0.0f;
+      if (v1) p1 = src.phi(a, r1, c1, x0 - 3 + c1, y0 - 3 + r1);
+      if (v2) p2 = src.phi(a, r2, c2, x0 - 3 + c2, y0 - 3 + r2);
+      if (v1) sPhi[r1 * B3X + c1] = p1;
+      if (v2) sPhi[r2 * B3X + c2] = p2;
+    } else {
+      for (int m = tid; m < R3; m += NT) {
+        int r, cc;
+        ring3(m, r, cc);
+        phi_node(r, cc);
       }
     }
   } else {
@@ -527,8 +549,30 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     if constexpr (kIn) src.f_node(a, oly, olx, ogx, ogy, f);
     else src.f_node(a, oly, olx, col(ogx), map_row(ogy, L.ny, L.wall), f);
   };
+  // kOwn on an inner tile: f of the thread's 1-ring node too (the threads
+  // that have one), so that pass 3 waits for no load
+  constexpr int R1 = F::N1 - NTILE;
+  constexpr bool kPreRing = kPre && kOwn && kIn && R1 <= NT;
+  const auto ring1 = [&](int m, int& ly1, int& lx1) {
+    if (m < 2 * B1X) {
+      ly1 = m < B1X ? 0 : TY + 1;
+      lx1 = m < B1X ? m : m - B1X;
+    } else {
+      const int q = m - 2 * B1X;
+      ly1 = 1 + (q >> 1);
+      lx1 = (q & 1) ? kTX + 1 : 0;
+    }
+  };
+  float fring[kPreRing ? 9 : 1];
   if constexpr (kPre && kOwn) {
     load_own_f(fpre);
+    if constexpr (kPreRing) {
+      if (tid < R1) {
+        int ly1, lx1;
+        ring1(tid, ly1, lx1);
+        src.f_ring1(a, ly1, lx1, x0 - 1 + lx1, y0 - 1 + ly1, fring);
+      }
+    }
   } else if constexpr (kPre) {
     const int ly = tid / B1X, lx = tid - ly * B1X;
     if constexpr (kIn) src.f_ring1(a, ly, lx, x0 - 1 + lx, y0 - 1 + ly, fpre);
@@ -657,19 +701,20 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     if constexpr (!kPre) load_own_f(fpre);
     own3 = pass3((oly + 1) * B1X + olx + 1, fpre);
     // the 1-ring: the rows above and below, then the columns left and right
-    for (int m = tid; m < N1 - NTILE; m += NT) {
-      int ly1, lx1;
-      if (m < 2 * B1X) {
-        ly1 = m < B1X ? 0 : TY + 1;
-        lx1 = m < B1X ? m : m - B1X;
-      } else {
-        const int q = m - 2 * B1X;
-        ly1 = 1 + (q >> 1);
-        lx1 = (q & 1) ? kTX + 1 : 0;
+    if constexpr (kPreRing) {
+      if (tid < R1) {
+        int ly1, lx1;
+        ring1(tid, ly1, lx1);
+        pass3(ly1 * B1X + lx1, fring);
       }
-      float f[9];
-      load_ring1(ly1 * B1X + lx1, f);
-      pass3(ly1 * B1X + lx1, f);
+    } else {
+      for (int m = tid; m < R1; m += NT) {
+        int ly1, lx1;
+        ring1(m, ly1, lx1);
+        float f[9];
+        load_ring1(ly1 * B1X + lx1, f);
+        pass3(ly1 * B1X + lx1, f);
+      }
     }
   } else {
     if constexpr (kPre) pass3(tid, fpre);
