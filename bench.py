@@ -488,7 +488,7 @@ def run_ours(args, case):
     l2x = (measure_l2_exceeding(args, dev, wall_x=wall_x)
            if ws == 1 and not args.no_l2x and case.nx * case.ny < (1 << 23) else None)
     # the patterns against this plain FP32 line (default workload, one GPU)
-    patterns = (measure_patterns(args, case, dev, value)
+    patterns = (measure_patterns(args, case, dev, value, l2x)
                 if ws == 1 and not args.no_patterns and args.storage == "fp32" and not wall_x
                 else None)
 
@@ -816,11 +816,13 @@ def measure_storage(args, case, dev, storage, steps):
             "state_status": dom.diagnostics()["status"]}
 
 
-def measure_patterns(args, case, dev, plain_value):
+def measure_patterns(args, case, dev, plain_value, l2x=None):
     """The three patterns against the plain FP32 step, measured in this run:
-    16-bit storage on the timed workload, the 256-instance batch against the
-    same instances launched one by one, and the adjoint of the 512 x 256
-    drop in shear (4000 steps, checkpoint every 200) against its forward."""
+    16-bit storage on the timed workload (and, when the line has its
+    L2-exceeding point, on that 2048 x 4096 grid against the FP32 point), the
+    256-instance batch against the same instances launched one by one, and
+    the adjoint of the 512 x 256 drop in shear (4000 steps, checkpoint every
+    200) against its forward."""
     import argparse as _ap
     out = {"plain_fp32": {"value": plain_value, "unit": "GLUPS"}}
 
@@ -834,6 +836,13 @@ def measure_patterns(args, case, dev, plain_value):
     def storage(st):
         r = measure_storage(args, case, dev, st, args.steps)
         r["vs_plain"] = r["value"] / plain_value
+        if l2x is not None:
+            big = measure_l2_exceeding(_ap.Namespace(**{**vars(args), "storage": st}), dev)
+            r["l2_exceeding"] = {"workload": big["workload"], "value": big["value"],
+                                 "unit": "GLUPS", "stage": big["stage"],
+                                 "roofline_frac": big["roofline_frac"],
+                                 "vs_plain": big["value"] / l2x["value"],
+                                 "state_status": big["state_status"]}
         return r
 
     def batch():
