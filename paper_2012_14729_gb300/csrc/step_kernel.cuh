@@ -519,7 +519,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
       }
     }
   } else {
-#pragma unroll 2
+#pragma unroll 3
     for (int k = tid; k < F::N3; k += NT) {
       const int r = k / B3X;
       phi_node(r, k - r * B3X);
@@ -718,6 +718,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     }
   } else {
     if constexpr (kPre) pass3(tid, fpre);
+#pragma unroll 2
     for (int k = kPre ? tid + NT : tid; k < N1; k += NT) {
       float f[9];
       load_ring1(k, f);
