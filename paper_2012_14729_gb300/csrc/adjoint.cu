@@ -463,9 +463,11 @@ __device__ __forceinline__ float stencil_T_tile(const float* b, int c, int y, co
 // ring lies inside the domain, off the wall rows and the periodic seams (no
 // wrap, no ghost terms).
 constexpr int kTW = 32, kTH = 8, kTS = kTW + 4, kTN = kTS * (kTH + 4);
-// 256 threads, six CTAs per SM (40 registers): measured faster than one
+// 256 threads, four CTAs per SM (64 registers; the 512 tiles of a 512 x 256
+// grid still fit one wave): measured faster than six CTAs per SM at 40
+// registers, than the same with the stage loops unrolled, and than one
 // thread per ring node (448 threads, three or four CTAs per SM)
-constexpr int kTailThreads = 256, kTailBlocks = 6;
+constexpr int kTailThreads = 256, kTailBlocks = 4;
 template <bool IN>
 __device__ __forceinline__ void tail_tile(const AdjArgs& A, float (*sw)[kTN], float (*sv)[kTN],
                                           int x0, int y0, double& db, double& dk, double& ds) {
