@@ -28,14 +28,14 @@ __device__ __forceinline__ void gather_item(const StepArgs& a, int form, unsigne
   using S = GatherSrc<ST, INNER>;
   const S src{};
   switch (form) {
-    case kSTF1: step_tile<kSTF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    case kSTF2: step_tile<kSTF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    case kCPF1: step_tile<kCPF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    case kCPF2: step_tile<kCPF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    case kPF1: step_tile<kPF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    case kPF2: step_tile<kPF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    case kCSF1: step_tile<kCSF1, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
-    default: step_tile<kCSF2, ST, NT, S, false, TY, false>(a, src, fs, x0, y0); break;
+    case kSTF1: step_tile<kSTF1, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    case kSTF2: step_tile<kSTF2, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    case kCPF1: step_tile<kCPF1, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    case kCPF2: step_tile<kCPF2, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    case kPF1: step_tile<kPF1, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    case kPF2: step_tile<kPF2, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    case kCSF1: step_tile<kCSF1, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
+    default: step_tile<kCSF2, ST, NT, S, false, TY, false, false>(a, src, fs, x0, y0); break;
   }
 }
 
@@ -46,14 +46,14 @@ __device__ __forceinline__ void run_item(const StepArgs& a, const StepArgs& ga, 
     static_assert(TY == kTY, "box staging is laid out for full tiles");
     const BoxSrc<ST> src{bx};
     switch (form) {
-      case kSTF1: step_tile<kSTF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      case kSTF2: step_tile<kSTF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      case kCPF1: step_tile<kCPF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      case kCPF2: step_tile<kCPF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      case kPF1: step_tile<kPF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      case kPF2: step_tile<kPF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      case kCSF1: step_tile<kCSF1, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
-      default: step_tile<kCSF2, ST, NT, BoxSrc<ST>, false, kTY, false>(a, src, fs, x0, y0); break;
+      case kSTF1: step_tile<kSTF1, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      case kSTF2: step_tile<kSTF2, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      case kCPF1: step_tile<kCPF1, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      case kCPF2: step_tile<kCPF2, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      case kPF1: step_tile<kPF1, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      case kPF2: step_tile<kPF2, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      case kCSF1: step_tile<kCSF1, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
+      default: step_tile<kCSF2, ST, NT, BoxSrc<ST>, false, kTY, false, false>(a, src, fs, x0, y0); break;
     }
   } else if (inner_tile<TY>(a.L, x0, y0)) {
     gather_item<ST, NT, true, TY>(a, form, fs, x0, y0);

@@ -421,8 +421,10 @@ __device__ __forceinline__ void collide_pair(const CollideConsts& k, float fi, f
 // adjoint reads (plane layout of the TapePlane enum, a.tape + plane * nx ny).
 // OWN (one collision node per thread only): keep the own node's populations
 // in registers between the passes (below).
+// NEXT (two collision nodes per thread): issue the second node's pulls before
+// the first node's collision (off where the extra live values would spill).
 template <int FORM, class ST, int NT, class SRC, bool TAPE = false, int TY = kTY,
-          bool OWN = kTX * TY == NT>
+          bool OWN = kTX * TY == NT, bool NEXT = true>
 __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, unsigned char* fs,
                                           int x0, int y0) {
   using F = Fields<FORM, TAPE, TY>;
@@ -776,6 +778,18 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
   }
 
   // ---- pass 4: collide and store on the tile --------------------------------
+  // two collision nodes per thread on an inner tile: the second node's pulls
+  // are issued before the first node's collision, so that they arrive while
+  // it runs (measured faster for STF-1, CPF and PF; the STF-2 and CSF forces
+  // then spill, and run slower)
+  constexpr bool kNext = NEXT && !kOwn && NPT == 2 && kIn && FORM != kSTF2 && FORM != kCSF1 &&
+                         FORM != kCSF2;
+  float fnx[kNext ? 9 : 1], hnx[kNext ? 9 : 1];
+  if constexpr (kNext) {
+    const int k1 = tid + NT, ly1 = k1 / kTX, lx1 = k1 - ly1 * kTX;
+    src.f_node(a, ly1, lx1, x0 + lx1, y0 + ly1, fnx);
+    src.h_node(a, ly1, lx1, x0 + lx1, y0 + ly1, hnx);
+  }
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
     const int k = tid + j * NT;
@@ -798,6 +812,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     if constexpr (kOwn) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i] = fpre[i];
+    } else if (kNext && j == 1) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = fnx[kNext ? i : 0];
     } else {
       src.f_node(a, ly, lx, gx, gy, f);
     }
@@ -863,6 +880,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& a, const SRC& src, uns
     if constexpr (kOwn) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) h[i] = hown[i];
+    } else if (kNext && j == 1) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i] = hnx[kNext ? i : 0];
     } else {
       src.h_node(a, ly, lx, gx, gy, h);
     }
