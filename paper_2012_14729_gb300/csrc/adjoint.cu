@@ -150,8 +150,8 @@ __device__ __forceinline__ float hb_full(const AdjArgs& A, int n, int i, int m, 
 }
 
 // streaming transpose + collision transpose (+ bounce-back terms); built for
-// 8 blocks per SM (64 registers): the kernel is bound by the latency of its
-// gathers, so more resident warps beat the few spilled registers
+// 7 blocks per SM (72 registers): the kernel is bound by the latency of its
+// gathers; measured faster than 8 blocks at 64 registers and than 6 at 80
 __global__ void __launch_bounds__(kAB, 7) k_adj_collide(const AdjArgs A) {
   ADJ_NODE
   const Phys& P = A.p;
