@@ -570,6 +570,9 @@ def main():
                     help="skip the 16-bit, batch and adjoint measurements of the default line")
     ap.add_argument("--ckpt-every", type=int, default=200,
                     help="adjoint workloads: checkpoint interval of the gradient run")
+    ap.add_argument("--batch-config", default=None,
+                    help="batch workloads: MODE:CTAS_PER_SM:ROWS instead of the autotuner's "
+                         "choice, e.g. gather:4:16")
     ap.add_argument("--no-l2x", action="store_true",
                     help="skip the extra 2048 x 4096 (larger than L2) measurement")
     args = ap.parse_args()
@@ -713,7 +716,13 @@ def measure_batch(args, clocks=True, ws=1, rank=0):
     nodes = sum(c.nx * c.ny for c in cases)
     b = pflbm.Batch(doms, stream=stream)
     b.step(1)
-    mode, cps, rows = b.autotune(3)
+    if getattr(args, "batch_config", None):
+        # a fixed configuration (e.g. to profile what the autotuner picks in a plain run)
+        m, c_, r_ = args.batch_config.split(":")
+        b.config(m, int(c_), int(r_))
+        mode, cps, rows = m, int(c_), int(r_)
+    else:
+        mode, cps, rows = b.autotune(3)
     b.graphs(True)
     b.step(args.warmup)
     b.synchronize()
