@@ -4,13 +4,14 @@
 // The forward intermediates of step t (pulled f, phi, grad phi, lap phi, mu,
 // the force, u, P, div(phi u), d_t(phi u)) are recorded by the taping step
 // (the fused step kernel with its tape output, step_kernel.cuh).  The reverse
-// of the step then runs as four one-thread-per-node kernels:
+// of the step then runs as two kernels:
 //   collide  streaming transpose (push, with the bounce-back terms) and the
-//            collision transpose of f and h;
-//   mid      transpose of div(phi u) and d_t(phi u), of the macroscopic
-//            relations (u, P, rho) and the pointwise part of the force;
-//   late     transposes of the force stencils and of the chemical potential;
-//   finish   transposes of grad phi and lap phi into the adjoint of phi.
+//            collision transpose of f and h, one thread per node;
+//   tail     on 32 x 8 tiles: the transpose of div(phi u) and d_t(phi u), of
+//            the macroscopic relations (u, P, rho) and the pointwise part of
+//            the force (tile + 2 ring), the transposes of the force stencils
+//            and of the chemical potential (tile + 1 ring), and those of
+//            grad phi and lap phi into the adjoint of phi (tile).
 // The transpose of each stencil is a gather over the nodes whose stencil reads
 // a node, directly or through a wall ghost (mirror rule with the field's
 // parity) or the periodic seam.  The adjoints of phi = sum h_i and of S, j
@@ -21,9 +22,6 @@
 // added to four accumulators.
 #include "step_kernel.cuh"
 
-#ifndef ADJ_TAIL_FUSED_MAX
-#define ADJ_TAIL_FUSED_MAX 262144
-#endif
 
 namespace pflbm {
 
@@ -580,80 +578,18 @@ __global__ void __launch_bounds__(kTailThreads, kTailBlocks) k_adj_tail(const Ad
   }
 }
 
-// The same three stages as separate one-thread-per-node kernels over the
-// whole grid, exchanging their values through the work planes.
-__global__ void __launch_bounds__(kAB) k_adj_mid(const AdjArgs A) {
-  ADJ_NODE
-  double dk = 0.0, ds = 0.0;
-  if (live) {
-    const Tail t = mid_node(A, n, x, y, k, true, dk, ds);
-    WKK(B_PHI, k) = t.phib;
-    WKK(B_GX, k) = t.Gxb;
-    WKK(B_GY, k) = t.Gyb;
-    WKK(B_MU, k) = t.mub;
-    WKK(B_L, k) = t.Lb;
-    WKK(B_W0, k) = t.w0;
-    WKK(B_W1, k) = t.w1;
-    WKK(B_W2, k) = t.w2;
-  }
-  acc_add(A.acc, 0.0, dk, 0.0, ds);
-}
-
-__global__ void __launch_bounds__(kAB) k_adj_late(const AdjArgs A) {
-  ADJ_NODE
-  double db = 0.0, dk = 0.0;
-  if (live) {
-    const Geo& g = A.g;
-    Tail v;
-    v.phib = WKK(B_PHI, k);
-    v.Gxb = WKK(B_GX, k);
-    v.Gyb = WKK(B_GY, k);
-    v.mub = WKK(B_MU, k);
-    v.Lb = WKK(B_L, k);
-    const float* w[3] = {WK(B_W0), WK(B_W1), WK(B_W2)};
-    const auto st = [&](int f, int axis, float parity) {
-      return stencil_T<false>(w[f], g, x, y, axis, parity);
-    };
-    late_node(A, n, k, v, st, db, dk);
-    WKK(B_PHI, k) = v.phib;
-    WKK(B_GX, k) = v.Gxb;
-    WKK(B_GY, k) = v.Gyb;
-    WKK(B_L, k) = v.Lb;
-  }
-  acc_add(A.acc, db, dk, 0.0, 0.0);
-}
-
-// grad phi, lap phi -> phi: the per-node adjoint of phi = sum h_i
-__global__ void __launch_bounds__(kAB) k_adj_finish(const AdjArgs A) {
-  ADJ_NODE
-  if (!live) return;
-  const Geo& g = A.g;
-  reinterpret_cast<float*>(A.aout)[4 * k + 3] =  // the PHI (w) component of SO(k)
-      WKK(B_PHI, k) + stencil_T<false>(WK(B_GX), g, x, y, 0, 1.0f) +
-      stencil_T<false>(WK(B_GY), g, x, y, 1, 1.0f) + stencil_T<true>(WK(B_L), g, x, y, 0, 1.0f);
-}
-
-// Grids up to this many nodes run the three stages after the collision
-// transpose as one tiled kernel (fewer launches where every kernel is
-// latency-bound); larger grids run them as three kernels (no ring
-// recomputation where the stages are bound by their bytes).  Measured on the
-// drop in shear: fused 20.2 vs 22.1 ms at 131 072 nodes, 68.3 vs 65.6 ms at
-// 524 288 nodes, 229 vs 216 ms at 2 097 152 nodes.
-constexpr long long kTailFusedMaxNodes = ADJ_TAIL_FUSED_MAX;
-
 // Reverse of one step: adjoint state at t + 1 (A.ain) -> at t (A.aout), with
 // the tape of step t.
+// The stages after the collision transpose run as one tiled kernel on every
+// grid (measured on the drop in shear against three one-thread-per-node
+// kernels exchanging their values through work planes: 4.5x against 4.6x the
+// forward at 131 072 nodes, 6.5x against 6.8x at 524 288, 6.2x against 6.3x
+// at 2 097 152).
 cudaError_t launch_adjoint_step(const AdjArgs& A, cudaStream_t s) {
   const dim3 grid((A.g.nx + kAB - 1) / kAB, A.g.ny);
   k_adj_collide<<<grid, kAB, 0, s>>>(A);
-  if ((long long)A.g.nx * A.g.ny <= kTailFusedMaxNodes) {
-    const dim3 tiles((A.g.nx + kTW - 1) / kTW, (A.g.ny + kTH - 1) / kTH);
-    k_adj_tail<<<tiles, kTailThreads, 0, s>>>(A);
-  } else {
-    k_adj_mid<<<grid, kAB, 0, s>>>(A);
-    k_adj_late<<<grid, kAB, 0, s>>>(A);
-    k_adj_finish<<<grid, kAB, 0, s>>>(A);
-  }
+  const dim3 tiles((A.g.nx + kTW - 1) / kTW, (A.g.ny + kTH - 1) / kTH);
+  k_adj_tail<<<tiles, kTailThreads, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -122,8 +122,8 @@ enum AdjPlane { AP_F0 = 0, AP_H0 = 9, AP_QX = 18, AP_QY, kAdjPlanes };
 constexpr int kAdjScalar = 4;  // floats of the per-node scalar block
 // Work planes of one reverse step.
 enum WorkPlane {
-  B_PHI, B_RHO, B_UX, B_UY, B_P, B_FX, B_FY, B_GX, B_GY, B_MU, B_DIV, B_DTX, B_DTY, B_L, B_W0,
-  B_W1, B_W2, kWorkPlanes
+  B_PHI, B_RHO, B_UX, B_UY, B_P, B_FX, B_FY, B_GX, B_GY, B_MU, B_DIV, B_DTX, B_DTY, B_L,
+  kWorkPlanes
 };
 struct AdjGeo {
   int nx, ny, wall;
@@ -142,7 +142,7 @@ struct AdjArgs {
 // setup_tape_step sets its kernel attributes and must precede a capture.
 cudaError_t setup_tape_step(int form);
 cudaError_t launch_tape_step(int form, const StepArgs& a, cudaStream_t s);
-// Reverse of one step: 4 kernels.
+// Reverse of one step: 2 kernels.
 cudaError_t launch_adjoint_step(const AdjArgs& A, cudaStream_t s);
 // Adjoint of the initial state h = h^eq(phi0, mu0, 0): dphi0 from A.ain.
 cudaError_t launch_adjoint_init(const AdjArgs& A, const float* phi0, float* dphi0,

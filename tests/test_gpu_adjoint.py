@@ -170,10 +170,11 @@ def test_legacy_stream_runs_without_graphs(pf):
     np.testing.assert_array_equal(out[0][2], out[1][2])
 
 
-def test_adjoint_on_a_grid_above_the_fused_tail_limit(pf, orc):
-    """640 x 420 nodes (more than the 262 144 up to which the last three
-    reverse stages run as one tiled kernel): the separate-kernel path against
-    central differences of the FP64 oracle."""
+def test_adjoint_on_a_larger_walled_grid(pf, orc):
+    """640 x 420 nodes (268 800, ragged in y for the reverse tail's 32 x 8
+    tiles), moving walls, gravity and a density contrast: the reverse sweep
+    on a grid of many tiles against central differences of the FP64
+    oracle."""
     import torch
     nx, ny, wall, form = 640, 420, True, "CSF1"
     phi0 = wl.drop(nx, ny, 60.0, 4.0, xc=301.7, yc=209.6, periodic_y=False).astype(np.float32)
